@@ -1,0 +1,314 @@
+"""Benchmark of the NENO6 Euler right-hand side on GB300.
+
+One step = one third-order SSP Runge-Kutta step of the whole grid: the CFL
+reduction and three fused right-hand-side evaluations (the hot path: ghost
+cells, Roe characteristic projection, LLF split, classifier, renormalised
+combination, back-projection, conservative difference, stage update).
+
+Default workload (N=1): 2D Euler, 2048 x 2048 periodic grid, seeded
+four-quadrant states with a sinusoidal density perturbation, FP64 path.
+Metric: Mcell-updates/s (cells x steps / s), higher is better.
+
+`--impl reference` times the FP64 CPU oracle on the same workload's
+structure (a bounded periodic crop per step) on this host's cores.
+
+Under torchrun (N > 1) every rank advances its own independent copy of the
+workload (weak scaling, no data-path collective); rank 0 prints one JSON
+line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2D Euler NENO6 RHS Mcell-updates/s: mixed-prec vs FP64 GPU, at stated L1 error"
+UNIT = "Mcell-updates/s"
+WEIGHTS = os.path.join(ROOT, "weights", "neno6_mlp_6x64x32x16x8x4.bin")
+SMS = 152
+
+
+# --------------------------------------------------------------- flop count
+def flops_per_cell_rhs(ndim=2):
+    """Algorithmic binary64 flops of one cell's right-hand side, counted from
+    the scheme's definition (fma = 2, every other + - * / sqrt = 1; max, |x|
+    and ReLU not counted).  Per face: Roe average and eigenvectors, per field
+    the projection of six cells (U and F), LLF split, two normalisations, two
+    classifier calls, two candidate sets, two renormalised combinations, the
+    sum of both sides; back-projection.  Per cell: primitives and fluxes, the
+    conservative difference.  2D: two faces per cell (one x, one y)."""
+    nv = 4 if ndim == 2 else 3
+    mlp = 2 * (6 * 64 + 64 * 32 + 32 * 16 + 16 * 8 + 8 * 4)    # 3104 fma
+    roe = 29 if ndim == 2 else 21
+    eig = 15 if ndim == 2 else 12
+    alpha = 12                                                # u_n -/+ c for the two acoustic fields
+    per_field = (6 * 2 * (1 + 2 * (nv - 1))                   # v = L.U_j, g = L.F_j
+                 + 6 * 6                                      # split: 2 fma + 2 mul per cell
+                 + 2 * 6                                      # 2 x 6 divisions (normalise)
+                 + 2 * mlp
+                 + 2 * 22                                     # candidates S0..S3, both sides
+                 + 2 * (3 + 4 + 8)                            # sum of d, 4 divisions, 4 fma
+                 + 1)                                         # g+ + g-
+    per_face = roe + eig + alpha + nv * per_field + nv * (1 + 2 * (nv - 1))
+    per_cell = 25 + nv * (5 if ndim == 2 else 2)
+    return ndim * per_face + per_cell
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+    import paper_2207_08500_gb300 as neno6
+    import synth
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    n = args.n
+    cfl = 0.4
+    weights = args.weights
+    solver = neno6.Neno6(ndim=2, nx=n, ny=n, bc=("periodic", "periodic"), precision="fp64",
+                         weights=weights)
+    U0 = synth.quadrants_2d(n, n)  # seeded, identical on every rank (weak scaling)
+    U = torch.from_numpy(U0).to(dev)
+    stream = torch.cuda.current_stream()
+    t_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        solver.step(U, cfl, t=t_dev)
+    torch.cuda.synchronize()
+    if solver.status():
+        raise RuntimeError("non-physical state during warm-up")
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        solver.step(U, cfl, t=t_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clock_info = clocks.stop()
+
+    # per-launch duration of the dominant kernel (the fused RHS), same
+    # workload and launch configuration, on the launching stream
+    dUdt = torch.empty_like(U)
+    reps = max(3, args.steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for r in range(reps):
+        solver.rhs(U, out=dUdt)
+        ev[r + 1].record(stream)
+    torch.cuda.synchronize()
+    rhs_ms = [ev[r].elapsed_time(ev[r + 1]) for r in range(reps)]
+    rhs_avg = sum(rhs_ms) / reps
+
+    # end to end through the C ABI with host buffers: H2D of the state, the
+    # step, D2H of the new state, every step
+    host = torch.from_numpy(U0.copy()).pin_memory()
+    out_host = torch.empty_like(host).pin_memory()
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        U.copy_(host, non_blocking=True)
+        solver.step(U, cfl, t=t_dev)
+        out_host.copy_(U, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    status = solver.status()
+
+    # max over ranks
+    vals = torch.tensor([ms, e2e_ms, rhs_avg], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_ms, rhs_avg = vals.tolist()
+
+    cells = n * n
+    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    e2e_value = cells * e2e_steps * world / (e2e_ms * 1e-3) / 1e6
+    fl = flops_per_cell_rhs(2) * cells
+    achieved = fl / (rhs_avg * 1e-3) / 1e12
+    peak = fp64_peak_tflops()
+    state_bytes = U.numel() * 8
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded four-quadrant Euler states, trained frozen classifier)",
+        "config": {"workload": "2D Euler 2048x2048 periodic, FP64 NENO6 RHS, SSP-RK3 (CFL 0.4)",
+                   "nx": n, "ny": n, "precision": "fp64", "step": "one SSP-RK3 step = 3 RHS",
+                   "l2": "inputs larger than L2 (state %d MB)" % (state_bytes >> 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "rhs_fp64_kernel",
+                     "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": "FP64 pipe: measured DFMA rate per SM per clock x 152 SMs x "
+                                    "2 flops x 2070 MHz (see DESIGN.md)",
+                     "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3)},
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clock_info,
+        "device_status": status,
+    }
+    return line
+
+
+def fp64_peak_tflops():
+    """FP64-pipe peak: DFMA issue rate per SM per clock (measured with a
+    microbenchmark, recorded in the design doc) x SMs x 2 flops x max SM clock."""
+    dfma_per_clk_sm = float(os.environ.get("NENO6_DFMA_PER_CLK_SM", "2.0"))
+    return round(dfma_per_clk_sm * SMS * 2 * 2070e6 / 1e12, 4)
+
+
+# ---------------------------------------------------------- oracle arm
+def oracle_timing(crop=64, reps=1):
+    """The FP64 CPU oracle on a periodic crop of the workload (same
+    generator, crop x crop cells): one SSP-RK3 step per rep."""
+    import oracle
+    import synth
+    from oracle.weights import Net
+    net = Net.load(WEIGHTS) if os.path.exists(WEIGHTS) else Net.random()
+    o = oracle.Oracle(ndim=2, nx=crop, ny=crop, net=net)
+    U = synth.quadrants_2d(crop, crop)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        U, _, _ = o.step(U, 0.4)
+    dt = time.perf_counter() - t0
+    return crop * crop * reps / dt / 1e6, dt
+
+
+def run_reference(args):
+    oracle_timing(16, 1)  # build + warm the oracle library
+    for _ in range(args.warmup):
+        oracle_timing(args.ref_crop, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_timing(args.ref_crop, 1)
+    dt = time.perf_counter() - t0
+    value = args.ref_crop ** 2 * args.steps / dt / 1e6
+    sample = "one SSP-RK3 step of a %dx%d periodic crop of the 2048^2 workload per step" % (
+        args.ref_crop, args.ref_crop)
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1, "impl": "reference",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "2D Euler 2048x2048 periodic, FP64 NENO6 RHS, "
+                                                    "SSP-RK3 (CFL 0.4)", "sample": sample},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--ref-crop", type=int, default=48)
+    ap.add_argument("--cpu-crop", type=int, default=96)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        v, secs = oracle_timing(args.cpu_crop, 1)
+        line["cpu_baseline"] = {
+            "value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one SSP-RK3 step (3 RHS) of a %dx%d periodic crop of the workload, "
+                      "%.1f s of CPU time" % (args.cpu_crop, args.cpu_crop, secs)}
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * neno6.h — C ABI of the NENO6 Euler right-hand side on one GB300 (sm_103a).
+ *
+ * NENO6 (Li, Fu & Adams, arXiv 2207.08500) is a six-point finite-difference
+ * reconstruction in which a small MLP decides which of four candidate
+ * stencils of incremental width enter the convex combination.  This library
+ * evaluates, for every cell face of a uniform 1D or 2D grid, the
+ * Roe-averaged characteristic projection, the local Lax-Friedrichs
+ * (Rusanov) flux split, the MLP stencil classification, the renormalised
+ * convex combination and the back-projection (Sec. 4.4, Algorithm 2), then
+ * the conservative difference (Eq. (approximateEq)) and the third-order SSP
+ * Runge-Kutta update (Sec. 4.4).
+ *
+ * Conventions for every entry point
+ *  - All array arguments are DEVICE pointers owned by the caller, unless a
+ *    comment says otherwise; the library never frees them.  They must be
+ *    8-byte aligned (16-byte for U / dUdt).
+ *  - States are float64 structure-of-arrays [nv][ny][nx], x fastest, with
+ *    nv = 3 conserved variables (rho, rho*u, E) in 1D and nv = 4
+ *    (rho, rho*u, rho*v, E) in 2D; ny = 1 in 1D.  Ghost cells are handled
+ *    inside the library (periodic wrap or zero-gradient copy per axis).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All work is enqueued on it; no call synchronises the host
+ *    except neno6_status and neno6_create/destroy.
+ *  - Every call returns NENO6_OK (0) or a negative NENO6_ERR_* code and
+ *    never throws or aborts; neno6_last_error gives a one-line message.
+ *    Conditions found on the device (a non-physical state) are latched in a
+ *    status word read by neno6_status; kernels never trap.
+ *  - A handle may be used from one host thread at a time.
+ */
+#ifndef NENO6_H
+#define NENO6_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define NENO6_OK 0
+#define NENO6_ERR_ARG (-1)         /* null pointer, bad enum, bad number   */
+#define NENO6_ERR_SHAPE (-2)       /* grid or batch size out of range      */
+#define NENO6_ERR_ALIGN (-3)       /* misaligned device pointer            */
+#define NENO6_ERR_WEIGHTS (-4)     /* weights file unreadable or corrupt   */
+#define NENO6_ERR_CUDA (-5)        /* a CUDA runtime call failed           */
+#define NENO6_ERR_NONPHYSICAL (-6) /* rho <= 0, p <= 0 or c^2 <= 0 seen    */
+#define NENO6_ERR_TIMEOUT (-7)     /* a bounded device wait gave up        */
+#define NENO6_ERR_UNSUPPORTED (-8) /* option not available for this handle */
+
+/* device status bits (neno6_status) */
+#define NENO6_STATUS_NONPHYSICAL_CELL 1 /* rho <= 0 or p <= 0 (or NaN)   */
+#define NENO6_STATUS_NONPHYSICAL_ROE 2  /* Roe-averaged c^2 <= 0         */
+
+/* neno6_config.precision */
+#define NENO6_FP64 0        /* everything in binary64 (bit-exact masks)    */
+#define NENO6_MIXED_BF16 1  /* MLP in bf16 on tensor cores, see below      */
+#define NENO6_MIXED_FP16 2  /* MLP in fp16 on tensor cores                 */
+
+/* neno6_config.bc[axis] */
+#define NENO6_BC_PERIODIC 0
+#define NENO6_BC_TRANSMISSIVE 1 /* zero-gradient ghost cells */
+
+/* neno6_config.linear_weights */
+#define NENO6_W_PAPER_OPT 0 /* d_k printed in Sec. 2.2 (fourth order)      */
+#define NENO6_W_SIXTH 1     /* (9/20, 3/10, 1/20, 1/5): sixth-order test   */
+
+/* neno6_config.mask_mode */
+#define NENO6_MASK_MLP 0        /* the classifier decides (the method)     */
+#define NENO6_MASK_ALL_SMOOTH 1 /* keep every stencil: the linear scheme   */
+#define NENO6_MASK_ALL_ROUGH 2  /* discard all: first-order upwind fallback */
+
+typedef struct neno6_config {
+  int ndim;           /* 1 or 2                                            */
+  int nx, ny;         /* interior cells, nx >= 1, ny >= 1 (ny = 1 in 1D)   */
+  double dx, dy;      /* cell sizes (> 0; dy unused in 1D)                 */
+  double gamma;       /* ratio of specific heats (> 1)                     */
+  int bc[2];          /* NENO6_BC_* for x and y                            */
+  int precision;      /* NENO6_FP64 | NENO6_MIXED_BF16 | NENO6_MIXED_FP16  */
+  int linear_weights; /* NENO6_W_*                                         */
+  int mask_mode;      /* NENO6_MASK_*                                      */
+} neno6_config;
+
+typedef struct neno6_handle neno6_handle;
+
+/*
+ * neno6_create — validate the configuration, read the classifier weights
+ * and prepare device state on the current CUDA device.
+ *   cfg           host pointer, copied.
+ *   weights_path  host string: weights file (magic "NENO6W01", int32 layer
+ *                 count L, int32 widths[L+1], per layer W[out][in] then
+ *                 b[out] as float64 little-endian, uint64 FNV-1a hash of the
+ *                 payload).  The parameters (w^l, b^l) of Sec. 3.1,
+ *                 Eq. (reconstuction).  Widths must be 6-64-32-16-8-4.
+ *   out           receives the handle (host pointer).
+ * Allocates device memory for the weights and the status word; the RK3
+ * stage buffers are allocated on the first neno6_step.
+ * Errors: ARG, SHAPE, WEIGHTS, UNSUPPORTED, CUDA.
+ */
+int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle** out);
+
+/* neno6_destroy — free the handle and its device memory (synchronises the
+ * device first).  NULL is accepted. */
+int neno6_destroy(neno6_handle* h);
+
+/* neno6_mask_bytes — size in bytes of a classifier mask array for this grid:
+ * x faces [nv][ny][nx+1] followed (2D) by y faces [nv][ny+1][nx]; face f of
+ * a line sits between cells f-1 and f.  One byte per (face, field): bits 0-3
+ * the "+" side's eta_0..eta_3, bits 4-7 the "-" side's (eta_k = 1: stencil
+ * S_k discarded).  Returns a negative code for a bad handle. */
+int64_t neno6_mask_bytes(const neno6_handle* h);
+
+/*
+ * neno6_rhs — semi-discrete right-hand side dU/dt = L(U).
+ * Sec. 4.4: x sweep then y sweep; per face the Roe characteristic
+ * projection, LLF split, classifier (Sec. 3.1), candidates and renormalised
+ * combination (Eqs. (convex), (TENOweight_renormalize), Algorithm 2), back-
+ * projection; then -(F_{i+1/2}-F_{i-1/2})/dx - (G_{j+1/2}-G_{j-1/2})/dy.
+ *   U         [nv][ny][nx] float64 in.
+ *   dUdt      [nv][ny][nx] float64 out (must not alias U).
+ *   mask_in   nullable; if given, the classifier is not run and these bits
+ *             (layout of neno6_mask_bytes) are used instead (frozen mask).
+ *   mask_out  nullable; receives the bits used.
+ * Errors: ARG, ALIGN, CUDA.  Non-physical states set the status word.
+ */
+int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mask_in,
+              uint8_t* mask_out, void* stream);
+
+/*
+ * neno6_step — one third-order SSP Runge-Kutta step in place (Sec. 4.4):
+ *   U1 = U + dt L(U);  U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ *   U  = 1/3 U + 2/3 (U2 + dt L(U2)),
+ * with dt = cfl / (max(|u|+c)/dx + max(|v|+c)/dy) computed on the device
+ * from U at the start of the step, clipped so that t + dt <= t_end when
+ * t_end > 0.
+ *   U      [nv][ny][nx] float64 in/out.
+ *   t_dev  nullable device float64 scalar holding t; advanced by dt.  When
+ *          NULL an internal time starting at 0 is used.
+ *   dt_dev nullable device float64 scalar receiving dt.
+ * Uses two library-owned stage buffers (allocated on first use).
+ * Errors: ARG, ALIGN, CUDA.
+ */
+int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_dev,
+               double* dt_dev, void* stream);
+
+/*
+ * neno6_classify — the classifier alone on a batch of stencils: Eq.
+ * (normalizainput) then Eqs. (reconstuction), (activationfunction); eta_k =
+ * [logit_k > 0] (sigmoid > 1/2, Sec. 3.1).
+ *   X        [n][6] float64 raw stencil values f_{i-2..i+3} (normalised here).
+ *   n        number of stencils, 0 <= n < 2^31.
+ *   eta_out  [n] uint8, bits 0-3 = eta_0..eta_3.
+ *   logits   nullable [n][4] float64.
+ * Errors: ARG, SHAPE, ALIGN, CUDA.
+ */
+int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out,
+                   double* logits, void* stream);
+
+/*
+ * neno6_status — synchronise `stream`, return the latched device status bits
+ * (NENO6_STATUS_*) in *device_status and clear them.  Returns
+ * NENO6_ERR_NONPHYSICAL when any bit was set, NENO6_ERR_CUDA when the stream
+ * reported an error, else NENO6_OK.
+ */
+int neno6_status(neno6_handle* h, int* device_status, void* stream);
+
+/* neno6_last_error — message of the last failed call on this handle (never
+ * NULL; "" when none).  With h == NULL: the last create failure. */
+const char* neno6_last_error(const neno6_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NENO6_H */

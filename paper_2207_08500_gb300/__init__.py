@@ -1,0 +1,186 @@
+"""Python binding of libneno6.so (the NENO6 Euler right-hand side on GB300).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream; the
+library itself sees plain device pointers (include/neno6.h).  There is no CPU
+fallback: importing works without a GPU, but constructing a solver requires
+the built library and a CUDA device, and fails loudly otherwise.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libneno6.so")
+DEFAULT_WEIGHTS = os.path.join(os.path.dirname(_HERE), "weights", "neno6_mlp_6x64x32x16x8x4.bin")
+
+OK = 0
+ERRORS = {-1: "ARG", -2: "SHAPE", -3: "ALIGN", -4: "WEIGHTS", -5: "CUDA", -6: "NONPHYSICAL",
+          -7: "TIMEOUT", -8: "UNSUPPORTED"}
+PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}
+BC = {"periodic": 0, "transmissive": 1}
+LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
+MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
+
+# Public C symbols declared in include/neno6.h (checked by the tests).
+EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
+           "neno6_classify", "neno6_status", "neno6_last_error")
+
+
+class Neno6Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("bc", ctypes.c_int * 2), ("precision", ctypes.c_int),
+                ("linear_weights", ctypes.c_int), ("mask_mode", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libneno6.so and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libneno6.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2207_08500_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, i64, u8p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+    lib.neno6_create.argtypes = [ctypes.POINTER(_Config), ctypes.c_char_p, ctypes.POINTER(vp)]
+    lib.neno6_destroy.argtypes = [vp]
+    lib.neno6_mask_bytes.argtypes = [vp]
+    lib.neno6_mask_bytes.restype = i64
+    lib.neno6_rhs.argtypes = [vp, dp, dp, u8p, u8p, vp]
+    lib.neno6_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp, dp, vp]
+    lib.neno6_classify.argtypes = [vp, dp, i64, u8p, dp, vp]
+    lib.neno6_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+    lib.neno6_last_error.argtypes = [vp]
+    lib.neno6_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Neno6:
+    """A grid + scheme configuration bound to the current CUDA device.
+
+    States are float64 CUDA tensors [nv, ny, nx] (nv = 3 in 1D, 4 in 2D) of
+    conserved variables (rho, rho u, [rho v], E).
+    """
+
+    def __init__(self, ndim=2, nx=64, ny=64, dx=None, dy=None, gamma=1.4,
+                 bc=("periodic", "periodic"), precision="fp64", linear_weights="paper",
+                 mask_mode="mlp", weights=DEFAULT_WEIGHTS):
+        if not torch.cuda.is_available():
+            raise RuntimeError("NENO6 needs a CUDA device; there is no CPU fallback")
+        lib = load_library()
+        if ndim == 1:
+            ny = 1
+        self.ndim, self.nx, self.ny = ndim, nx, ny
+        self.nv = 4 if ndim == 2 else 3
+        c = _Config()
+        c.ndim, c.nx, c.ny = ndim, nx, ny
+        c.dx = 1.0 / nx if dx is None else dx
+        c.dy = 1.0 / ny if dy is None else dy
+        c.gamma = gamma
+        c.bc[0], c.bc[1] = BC[bc[0]], BC[bc[1]]
+        c.precision = PRECISION[precision]
+        c.linear_weights = LINEAR_WEIGHTS[linear_weights]
+        c.mask_mode = MASK_MODE[mask_mode]
+        self.config = c
+        self.weights = weights
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        rc = lib.neno6_create(ctypes.byref(c), os.fsencode(weights), ctypes.byref(h))
+        if rc != OK:
+            raise Neno6Error(rc, lib.neno6_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.neno6_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            raise Neno6Error(rc, self._lib.neno6_last_error(self._h).decode())
+
+    @property
+    def shape(self):
+        return (self.nv, self.ny, self.nx)
+
+    @property
+    def mask_bytes(self):
+        return int(self._lib.neno6_mask_bytes(self._h))
+
+    def _state(self, U, name="U"):
+        if not (U.is_cuda and U.dtype == torch.float64 and U.is_contiguous()
+                and tuple(U.shape) == self.shape):
+            raise ValueError("%s must be a contiguous float64 CUDA tensor of shape %s"
+                             % (name, self.shape))
+        return U
+
+    def rhs(self, U, mask_in=None, want_mask=False, out=None):
+        """dU/dt = L(U); optionally with a frozen mask (mask_in) and/or the
+        classifier mask of this evaluation (want_mask)."""
+        U = self._state(U)
+        out = torch.empty_like(U) if out is None else self._state(out, "out")
+        mask = None
+        if want_mask:
+            mask = torch.empty(self.mask_bytes, dtype=torch.uint8, device=U.device)
+        if mask_in is not None:
+            assert mask_in.dtype == torch.uint8 and mask_in.numel() == self.mask_bytes
+            mask_in = mask_in.contiguous()
+        self._check(self._lib.neno6_rhs(self._h, _ptr(U), _ptr(out), _ptr(mask_in), _ptr(mask),
+                                        _stream()))
+        return (out, mask) if want_mask else out
+
+    def step(self, U, cfl, t_end=0.0, t=None, dt=None):
+        """One SSP-RK3 step of U in place.  t / dt: optional float64 CUDA
+        scalars (time, advanced on the device; dt of the step)."""
+        U = self._state(U)
+        self._check(self._lib.neno6_step(self._h, _ptr(U), float(cfl), float(t_end), _ptr(t),
+                                         _ptr(dt), _stream()))
+        return U
+
+    def classify(self, X, want_logits=False):
+        """Classifier bits (and logits) of raw stencils X [n, 6] float64."""
+        assert X.is_cuda and X.dtype == torch.float64 and X.shape[-1] == 6
+        X = X.contiguous()
+        n = X.shape[0]
+        eta = torch.empty(n, dtype=torch.uint8, device=X.device)
+        logits = torch.empty((n, 4), dtype=torch.float64, device=X.device) if want_logits else None
+        self._check(self._lib.neno6_classify(self._h, _ptr(X), n, _ptr(eta), _ptr(logits),
+                                             _stream()))
+        return (eta, logits) if want_logits else eta
+
+    def status(self):
+        """Synchronise the current stream and return (and clear) the device
+        status bits (1: non-physical cell, 2: non-physical Roe state)."""
+        v = ctypes.c_int(0)
+        rc = self._lib.neno6_status(self._h, ctypes.byref(v), _stream())
+        if rc not in (OK, -6):
+            self._check(rc)
+        return v.value

@@ -1,0 +1,340 @@
+// C ABI of the NENO6 library (declared in include/neno6.h): handle life
+// cycle, weights-file loading, argument checks and kernel launches.  Nothing
+// here throws across the ABI; errors are returned as NENO6_ERR_* codes with a
+// message kept on the handle.
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/neno6.h"
+#include "internal.h"
+
+using namespace neno6;
+
+struct neno6_handle {
+  neno6_config cfg;
+  int nv = 0;
+  int device = 0;
+  NetF64 net;                 // host copy of the classifier parameters
+  double d[4];                // linear weights
+  double cand[4][4];          // candidate coefficients
+  double wtab[16][4];         // renormalised weights per mask pattern
+  int* d_status = nullptr;    // device status word
+  unsigned long long* d_smax = nullptr;  // [2] CFL maxima
+  double* d_dt = nullptr;     // dt of the current step
+  double* d_t = nullptr;      // internal time (neno6_step with t_dev == NULL)
+  double* d_stage = nullptr;  // two RK3 stage states (lazily allocated)
+  size_t state_elems = 0;
+  RhsParamsF64 rhs_params;        // launch parameter blocks (copied at launch)
+  ClassifyParamsF64 cls_params;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+int fail(neno6_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(neno6_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, NENO6_ERR_CUDA, m);
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// FNV-1a 64-bit over the payload (weights-file integrity check).
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+  uint64_t h = 0xCBF29CE484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001B3ull;
+  }
+  return h;
+}
+
+int32_t rd_i32(const unsigned char* p) {
+  uint32_t v = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+  int32_t r;
+  std::memcpy(&r, &v, 4);
+  return r;
+}
+
+uint64_t rd_u64(const unsigned char* p) {
+  uint64_t v = 0;
+  for (int i = 7; i >= 0; --i) v = (v << 8) | p[i];
+  return v;
+}
+
+double rd_f64(const unsigned char* p) {
+  uint64_t v = rd_u64(p);
+  double d;
+  std::memcpy(&d, &v, 8);
+  return d;
+}
+
+int load_weights(const char* path, NetF64& net, std::string& msg) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    msg = std::string("cannot open weights file ") + path;
+    return NENO6_ERR_WEIGHTS;
+  }
+  std::vector<unsigned char> buf;
+  unsigned char tmp[65536];
+  size_t n;
+  while ((n = std::fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
+  std::fclose(f);
+  const size_t nparams = kNetParams;
+  const size_t expect = 8 + 4 + 4 * 6 + 8 * nparams + 8;
+  if (buf.size() < 16 || std::memcmp(buf.data(), "NENO6W01", 8) != 0) {
+    msg = "weights file: bad magic";
+    return NENO6_ERR_WEIGHTS;
+  }
+  const int32_t nl = rd_i32(&buf[8]);
+  if (nl != 5 || buf.size() != expect) {
+    msg = "weights file: only the 6-64-32-16-8-4 classifier is supported";
+    return NENO6_ERR_WEIGHTS;
+  }
+  for (int l = 0; l <= 5; ++l)
+    if (rd_i32(&buf[12 + 4 * l]) != kNetWidths[l]) {
+      msg = "weights file: widths are not 6-64-32-16-8-4";
+      return NENO6_ERR_WEIGHTS;
+    }
+  const size_t payload = buf.size() - 16;
+  if (fnv1a64(&buf[8], payload) != rd_u64(&buf[buf.size() - 8])) {
+    msg = "weights file: checksum mismatch";
+    return NENO6_ERR_WEIGHTS;
+  }
+  const unsigned char* p = &buf[12 + 4 * 6];
+  for (size_t i = 0; i < nparams; ++i) net.p[i] = rd_f64(p + 8 * i);
+  return NENO6_OK;
+}
+
+void fill_tables(neno6_handle* h) {
+  if (h->cfg.linear_weights == NENO6_W_SIXTH) {
+    h->d[0] = 9.0 / 20.0;
+    h->d[1] = 3.0 / 10.0;
+    h->d[2] = 1.0 / 20.0;
+    h->d[3] = 1.0 / 5.0;
+  } else {  // Sec. 2.2 / Sec. 4 (TENO6-opt optimal weights)
+    h->d[0] = 0.4294317718960898;
+    h->d[1] = 0.1727270875843552;
+    h->d[2] = 0.0855682281039113;
+    h->d[3] = 0.312272912415645;
+  }
+  // Reconstruction of h(x_{i+1/2}) from point values acting as cell averages
+  // (Eqs. (definitionEq), (approximatepolynomial)) on S0 = {i-1,i,i+1},
+  // S1 = {i,i+1,i+2}, S2 = {i-2,i-1,i}, S3 = {i,i+1,i+2,i+3}.
+  const double c[4][4] = {{-1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
+                          {1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
+                          {1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0},
+                          {1.0 / 4.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0}};
+  std::memcpy(h->cand, c, sizeof c);
+  // Eq. (TENOweight_renormalize): w_k = d_k delta_k / sum_k d_k delta_k,
+  // the sum taken over the kept stencils in k order.
+  for (int eta = 0; eta < 16; ++eta) {
+    double D = 0.0;
+    for (int k = 0; k < 4; ++k)
+      if (!((eta >> k) & 1)) D = D + h->d[k];
+    for (int k = 0; k < 4; ++k) h->wtab[eta][k] = (!((eta >> k) & 1) && D != 0.0) ? h->d[k] / D : 0.0;
+  }
+}
+
+void fill_rhs_args(const neno6_handle* h, RhsArgs& a) {
+  std::memset(&a, 0, sizeof a);
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.bcx = h->cfg.bc[0];
+  a.bcy = h->cfg.bc[1];
+  a.dx = h->cfg.dx;
+  a.dy = h->cfg.dy;
+  a.gamma = h->cfg.gamma;
+  a.gm1 = h->cfg.gamma - 1.0;
+  a.third = 1.0 / 3.0;
+  a.two_thirds = 2.0 / 3.0;
+  a.mask_mode = h->cfg.mask_mode;
+  a.status = h->d_status;
+  std::memcpy(a.cand, h->cand, sizeof a.cand);
+  std::memcpy(a.wtab, h->wtab, sizeof a.wtab);
+}
+
+}  // namespace
+
+extern "C" {
+
+int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle** out) {
+  if (!cfg || !weights_path || !out) return fail(nullptr, NENO6_ERR_ARG, "null argument");
+  *out = nullptr;
+  const neno6_config& c = *cfg;
+  if (c.ndim != 1 && c.ndim != 2) return fail(nullptr, NENO6_ERR_ARG, "ndim must be 1 or 2");
+  if (c.nx < 1 || c.ny < 1 || (c.ndim == 1 && c.ny != 1))
+    return fail(nullptr, NENO6_ERR_SHAPE, "need nx >= 1, ny >= 1 (ny == 1 in 1D)");
+  if ((long long)c.nx * c.ny > (1ll << 34) || c.nx > (1 << 30) || c.ny > (1 << 30))
+    return fail(nullptr, NENO6_ERR_SHAPE, "grid too large");
+  if (!(c.dx > 0.0) || (c.ndim == 2 && !(c.dy > 0.0)) || !(c.gamma > 1.0))
+    return fail(nullptr, NENO6_ERR_ARG, "need dx, dy > 0 and gamma > 1");
+  for (int k = 0; k < 2; ++k)
+    if (c.bc[k] != NENO6_BC_PERIODIC && c.bc[k] != NENO6_BC_TRANSMISSIVE)
+      return fail(nullptr, NENO6_ERR_ARG, "bad boundary condition");
+  if (c.linear_weights != NENO6_W_PAPER_OPT && c.linear_weights != NENO6_W_SIXTH)
+    return fail(nullptr, NENO6_ERR_ARG, "bad linear_weights");
+  if (c.mask_mode < NENO6_MASK_MLP || c.mask_mode > NENO6_MASK_ALL_ROUGH)
+    return fail(nullptr, NENO6_ERR_ARG, "bad mask_mode");
+  if (c.precision != NENO6_FP64 && c.precision != NENO6_MIXED_BF16 && c.precision != NENO6_MIXED_FP16)
+    return fail(nullptr, NENO6_ERR_ARG, "bad precision");
+  if (c.precision != NENO6_FP64)
+    return fail(nullptr, NENO6_ERR_UNSUPPORTED, "mixed precision is not available in this build");
+
+  neno6_handle* h = new (std::nothrow) neno6_handle();
+  if (!h) return fail(nullptr, NENO6_ERR_ARG, "out of host memory");
+  h->cfg = c;
+  h->nv = c.ndim == 2 ? 4 : 3;
+  std::string msg;
+  int rc = load_weights(weights_path, h->net, msg);
+  if (rc != NENO6_OK) {
+    delete h;
+    return fail(nullptr, rc, msg);
+  }
+  fill_tables(h);
+  h->state_elems = (size_t)h->nv * c.nx * c.ny;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_smax, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_dt, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_t, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_t, 0, sizeof(double));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    std::string m = std::string("device setup: ") + cudaGetErrorString(e);
+    neno6_destroy(h);
+    return fail(nullptr, NENO6_ERR_CUDA, m);
+  }
+  *out = h;
+  return NENO6_OK;
+}
+
+int neno6_destroy(neno6_handle* h) {
+  if (!h) return NENO6_OK;
+  cudaDeviceSynchronize();
+  cudaFree(h->d_status);
+  cudaFree(h->d_smax);
+  cudaFree(h->d_dt);
+  cudaFree(h->d_t);
+  cudaFree(h->d_stage);
+  delete h;
+  return NENO6_OK;
+}
+
+int64_t neno6_mask_bytes(const neno6_handle* h) {
+  if (!h) return NENO6_ERR_ARG;
+  const int64_t nx = h->cfg.nx, ny = h->cfg.ny, nv = h->nv;
+  int64_t n = nv * ny * (nx + 1);
+  if (h->cfg.ndim == 2) n += nv * (ny + 1) * nx;
+  return n;
+}
+
+int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mask_in,
+              uint8_t* mask_out, void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (!U || !dUdt) return fail(h, NENO6_ERR_ARG, "rhs: null state pointer");
+  if (!aligned(U, 16) || !aligned(dUdt, 16)) return fail(h, NENO6_ERR_ALIGN, "rhs: U/dUdt must be 16-byte aligned");
+  if ((const void*)U == (const void*)dUdt) return fail(h, NENO6_ERR_ARG, "rhs: dUdt must not alias U");
+  RhsParamsF64& p = h->rhs_params;
+  fill_rhs_args(h, p.a);
+  p.a.U = U;
+  p.a.out = dUdt;
+  p.a.mask_in = mask_in;
+  p.a.mask_out = mask_out;
+  if (mask_in) p.a.mask_mode = kMaskGiven;
+  p.a.stage = 0;
+  p.net = h->net;
+  cudaError_t e = launch_rhs_fp64(h->cfg.ndim, p, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rhs launch");
+  return NENO6_OK;
+}
+
+int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_dev, double* dt_dev,
+               void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (!U) return fail(h, NENO6_ERR_ARG, "step: null state pointer");
+  if (!aligned(U, 16)) return fail(h, NENO6_ERR_ALIGN, "step: U must be 16-byte aligned");
+  if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step: need cfl > 0, t_end >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!h->d_stage) {
+    cudaError_t e = cudaMalloc(&h->d_stage, 2 * h->state_elems * sizeof(double));
+    if (e != cudaSuccess) {
+      h->d_stage = nullptr;
+      return cuda_fail(h, e, "step: stage buffers");
+    }
+  }
+  double* S1 = h->d_stage;
+  double* S2 = h->d_stage + h->state_elems;
+  cudaError_t e = launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
+                                    h->d_status, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step: cfl reduction");
+  RhsParamsF64& p = h->rhs_params;
+  fill_rhs_args(h, p.a);
+  p.a.smax = h->d_smax;
+  p.a.dt_dev = h->d_dt;
+  p.a.t_dev = t_dev ? t_dev : h->d_t;
+  p.a.dt_user = dt_dev;
+  p.a.cfl = cfl;
+  p.a.t_end = t_end;
+  p.a.U0 = U;
+  p.net = h->net;
+  const double* in[3] = {U, S1, S2};
+  double* outp[3] = {S1, S2, U};
+  for (int st = 1; st <= 3; ++st) {
+    p.a.stage = st;
+    p.a.U = in[st - 1];
+    p.a.out = outp[st - 1];
+    e = launch_rhs_fp64(h->cfg.ndim, p, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step: stage launch");
+  }
+  return NENO6_OK;
+}
+
+int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out, double* logits,
+                   void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (n < 0 || n >= (1ll << 31)) return fail(h, NENO6_ERR_SHAPE, "classify: need 0 <= n < 2^31");
+  if (n == 0) return NENO6_OK;
+  if (!X || !eta_out) return fail(h, NENO6_ERR_ARG, "classify: null pointer");
+  if (!aligned(X, 8) || (logits && !aligned(logits, 8))) return fail(h, NENO6_ERR_ALIGN, "classify: misaligned");
+  ClassifyParamsF64& p = h->cls_params;
+  p.X = X;
+  p.eta = eta_out;
+  p.logits = logits;
+  p.n = n;
+  p.net = h->net;
+  cudaError_t e = launch_classify_fp64(p, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "classify launch");
+  return NENO6_OK;
+}
+
+int neno6_status(neno6_handle* h, int* device_status, void* stream) {
+  if (!h || !device_status) return NENO6_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status");
+  *device_status = v;
+  if (v) return fail(h, NENO6_ERR_NONPHYSICAL, "non-physical state seen on the device");
+  return NENO6_OK;
+}
+
+const char* neno6_last_error(const neno6_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

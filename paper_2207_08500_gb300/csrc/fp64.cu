@@ -1,0 +1,594 @@
+// FP64 path of the NENO6 Euler right-hand side (Li, Fu & Adams, arXiv
+// 2207.08500): one fused kernel per RHS evaluation (optionally with the SSP-RK3
+// stage combination as its epilogue), the batched classifier, and the CFL
+// reduction.
+//
+// Every binary64 operation is written with an explicit round-to-nearest
+// intrinsic (__dadd_rn, __dmul_rn, __fma_rn, __ddiv_rn, __dsqrt_rn, ...) in the
+// fixed order the scheme is specified in, so the compiler can neither contract
+// nor reorder it; the classifier masks are therefore a deterministic function
+// of the state, identical on any IEEE-754 implementation of that order.
+//
+// Design (GB300): binary64 arithmetic runs on the SM's FP64 pipe, and the
+// classifier (3104 multiply-adds per call, 16 calls per cell and RHS) is ~97 %
+// of the work, so this kernel is bound by that pipe.  Each CTA owns a tile of
+// cells, stages the tile plus a 3-cell halo (periodic wrap or zero-gradient
+// copy done in the load) and every per-cell quantity in shared memory once,
+// then runs one work item per (face, characteristic field) with four lanes
+// per face.  Classifier weights live in the kernel's parameter block
+// (constant bank), so the multiply-adds take the weight as a constant operand
+// and the warp reads it by broadcast.  Cheap comparisons (ReLU, max, |x|) are
+// done on the integer pipe on the bit patterns to keep the FP64 pipe for the
+// arithmetic.
+#include "internal.h"
+
+namespace neno6 {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int NDIM>
+struct Geom;
+template <>
+struct Geom<2> {
+  static constexpr int TX = 32, TY = 16, HY = 3, NV = 4;
+  static constexpr int SX = TX + 6, SY = TY + 6;
+  static constexpr int NXF = TY * (TX + 1);  // x faces of a tile
+  static constexpr int NYF = (TY + 1) * TX;  // y faces of a tile
+};
+template <>
+struct Geom<1> {
+  static constexpr int TX = 63, TY = 1, HY = 0, NV = 3;
+  static constexpr int SX = TX + 6, SY = 1;
+  static constexpr int NXF = TX + 1;
+  static constexpr int NYF = 0;
+};
+
+// Per-cell arrays staged in shared memory (structure of arrays).
+template <int NV>
+struct CellArrays {
+  static constexpr int U = 0;                // NV conserved variables
+  static constexpr int u = NV, v = NV + 1, c = NV + 2, H = NV + 3, s = NV + 4;
+  static constexpr int Fx = NV + 5;          // NV x-fluxes
+  static constexpr int Fy = Fx + NV;         // NV y-fluxes (2D)
+  static constexpr int N = Fy + NV;
+};
+
+// Per-thread slot parked in shared memory while the classifier runs (keeps
+// the stencils and the R row out of registers): "+" stencil, mirrored "-"
+// stencil, R row.
+constexpr int kPark = 16;
+
+template <int NDIM>
+constexpr size_t rhs_smem_bytes() {
+  using G = Geom<NDIM>;
+  return sizeof(double) * (size_t(CellArrays<G::NV>::N) * G::SX * G::SY +
+                           size_t(G::NV) * G::TY * (G::TX + 1) +
+                           size_t(G::NV) * (G::TY + 1) * G::TX + size_t(kPark) * kThreads);
+}
+
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > 0 for every non-NaN x (sign bit clear and not +0).
+__device__ __forceinline__ bool gt0(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ double relu(double x) { return gt0(x) ? x : 0.0; }
+__device__ __forceinline__ double dabs(double x) {
+  return __longlong_as_double(dbits(x) & 0x7fffffffffffffffLL);
+}
+// max of two non-negative values (bit patterns order like the values).
+__device__ __forceinline__ double dmax_nn(double a, double b) { return dbits(b) > dbits(a) ? b : a; }
+
+__device__ __forceinline__ int wrap_index(int i, int n, int bc) {
+  if (bc == 0) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Classifier 6-64-32-16-8-4 of Sec. 3.1 on a normalised stencil.  Eq.
+// (reconstuction): every output of a layer is its bias followed by an fma
+// chain over the layer's inputs in ascending order; ReLU (Eq.
+// (activationfunction)) on hidden layers.  Layers 1+2 and 3+4 are fused: each
+// hidden unit of layer 1 (3) is completed and immediately accumulated into
+// all sums of layer 2 (4), which keeps every sum's term order unchanged while
+// holding ~40 values live instead of ~100.  Parameters are packed per layer
+// as W[out][in] then b[out]: offsets 0/384, 448/2496, 2528/3040, 3056/3184,
+// 3192/3224.  Returns eta bits (logit > 0 <=> sigmoid > 1/2 <=> discard).
+__device__ __forceinline__ unsigned mlp64(const double* __restrict__ W, const double* x, double* z) {
+  double a2[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) a2[o] = W[2496 + o];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    double h = W[384 + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h = __fma_rn(W[i * 6 + k], x[k], h);
+    h = relu(h);
+#pragma unroll
+    for (int o = 0; o < 32; ++o) a2[o] = __fma_rn(W[448 + o * 64 + i], h, a2[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 32; ++o) a2[o] = relu(a2[o]);
+  double a4[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) a4[o] = W[3184 + o];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    double h = W[3040 + j];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) h = __fma_rn(W[2528 + j * 32 + i], a2[i], h);
+    h = relu(h);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) a4[o] = __fma_rn(W[3056 + o * 16 + j], h, a4[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) a4[o] = relu(a4[o]);
+  unsigned eta = 0;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    double acc = W[3224 + o];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc = __fma_rn(W[3192 + o * 8 + i], a4[i], acc);
+    z[o] = acc;
+    eta |= (gt0(acc) ? 1u : 0u) << o;
+  }
+  return eta;
+}
+
+// Eq. (normalizainput): divide by max(|s_0|, ..., |s_5|, 1).  s/1 == s
+// exactly, so the division is skipped when the maximum is 1.
+__device__ __forceinline__ void normalise6(const double* s, double* x) {
+  double m = 1.0;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) m = dmax_nn(m, dabs(s[j]));
+  if (dbits(m) == dbits(1.0)) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) x[j] = s[j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) x[j] = __ddiv_rn(s[j], m);
+  }
+}
+
+// Candidate fluxes (Eqs. (definitionEq)/(approximatepolynomial)) on the
+// stencil s_0..s_5 = i-2..i+3 and their renormalised convex combination
+// (Eqs. (TENOweight_renormalize), (convex)); Algorithm 2's first-order
+// fallback when all four are discarded.
+__device__ __forceinline__ double combine64(const RhsArgs& a, const double* s, unsigned eta) {
+  if (eta == 15u) return s[2];
+  double f[4];
+  f[0] = __fma_rn(a.cand[0][2], s[3], __fma_rn(a.cand[0][1], s[2], __dmul_rn(a.cand[0][0], s[1])));
+  f[1] = __fma_rn(a.cand[1][2], s[4], __fma_rn(a.cand[1][1], s[3], __dmul_rn(a.cand[1][0], s[2])));
+  f[2] = __fma_rn(a.cand[2][2], s[2], __fma_rn(a.cand[2][1], s[1], __dmul_rn(a.cand[2][0], s[0])));
+  f[3] = __fma_rn(a.cand[3][3], s[5],
+                  __fma_rn(a.cand[3][2], s[4],
+                           __fma_rn(a.cand[3][1], s[3], __dmul_rn(a.cand[3][0], s[2]))));
+  double g = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (!((eta >> k) & 1u)) g = __fma_rn(a.wtab[eta][k], f[k], g);
+  return g;
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_constant__ RhsParamsF64 P) {
+  using G = Geom<NDIM>;
+  using CA = CellArrays<G::NV>;
+  constexpr int NV = G::NV, SX = G::SX, SY = G::SY, NC = SX * SY;
+  constexpr int TX = G::TX, TY = G::TY;
+  extern __shared__ double smem[];
+  double* C = smem;                        // [CA::N][NC]
+  double* sFx = smem + CA::N * NC;         // [NV][TY][TX+1]
+  double* sFy = sFx + NV * TY * (TX + 1);  // [NV][TY+1][TX]
+  double* park = sFy + NV * (TY + 1) * TX + threadIdx.x;  // [kPark][kThreads]
+  const RhsArgs& a = P.a;
+  const double* __restrict__ net = P.net.p;
+  const int nx = a.nx, ny = a.ny;
+  const size_t plane = (size_t)nx * ny;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const double gm1 = a.gm1, gamma = a.gamma;
+
+  // ---- 1. tile + halo (ghost cells by wrap / clamp) and per-cell quantities
+  for (int e = threadIdx.x; e < NC; e += kThreads) {
+    const int bx = e % SX, by = e / SX;
+    const int gi = wrap_index(i0 - 3 + bx, nx, a.bcx);
+    const int gj = NDIM == 2 ? wrap_index(j0 - G::HY + by, ny, a.bcy) : 0;
+    const size_t g = (size_t)gj * nx + gi;
+    double U[NV];
+#pragma unroll
+    for (int n = 0; n < NV; ++n) {
+      U[n] = a.U[n * plane + g];
+      C[(CA::U + n) * NC + e] = U[n];
+    }
+    const double rho = U[0], E = U[NV - 1];
+    const double u = __ddiv_rn(U[1], rho);
+    double v = 0.0, q;
+    if (NDIM == 2) {
+      v = __ddiv_rn(U[2], rho);
+      q = __fma_rn(v, v, __dmul_rn(u, u));
+    } else {
+      q = __dmul_rn(u, u);
+    }
+    const double p = __dmul_rn(gm1, __dsub_rn(E, __dmul_rn(0.5, __dmul_rn(rho, q))));
+    const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+    const double Ep = __dadd_rn(E, p);
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.status, 1);
+    C[CA::u * NC + e] = u;
+    C[CA::v * NC + e] = v;
+    C[CA::c * NC + e] = c;
+    C[CA::H * NC + e] = __ddiv_rn(Ep, rho);
+    C[CA::s * NC + e] = __dsqrt_rn(rho);
+    if (NDIM == 2) {
+      C[(CA::Fx + 0) * NC + e] = U[1];
+      C[(CA::Fx + 1) * NC + e] = __fma_rn(U[1], u, p);
+      C[(CA::Fx + 2) * NC + e] = __dmul_rn(U[2], u);
+      C[(CA::Fx + 3) * NC + e] = __dmul_rn(Ep, u);
+      C[(CA::Fy + 0) * NC + e] = U[2];
+      C[(CA::Fy + 1) * NC + e] = __dmul_rn(U[1], v);
+      C[(CA::Fy + 2) * NC + e] = __fma_rn(U[2], v, p);
+      C[(CA::Fy + 3) * NC + e] = __dmul_rn(Ep, v);
+    } else {
+      C[(CA::Fx + 0) * NC + e] = U[1];
+      C[(CA::Fx + 1) * NC + e] = __fma_rn(U[1], u, p);
+      C[(CA::Fx + 2) * NC + e] = __dmul_rn(Ep, u);
+    }
+  }
+
+  // dt of an RK3 step (stage 1 computes it from max(|u|+c), max(|v|+c)).
+  double dt = 0.0;
+  if (a.stage == 1) {
+    const double sx = __longlong_as_double((long long)a.smax[0]);
+    double s = __ddiv_rn(sx, a.dx);
+    if (NDIM == 2) s = __dadd_rn(s, __ddiv_rn(__longlong_as_double((long long)a.smax[1]), a.dy));
+    dt = __ddiv_rn(a.cfl, s);
+    const double t = *a.t_dev;
+    if (a.t_end > 0.0 && __dadd_rn(t, dt) > a.t_end) dt = __dsub_rn(a.t_end, t);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+      *a.dt_dev = dt;
+      if (a.dt_user) *a.dt_user = dt;
+    }
+  } else if (a.stage >= 2) {
+    dt = *a.dt_dev;
+    if (a.stage == 3 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+      *a.t_dev = __dadd_rn(*a.t_dev, dt);
+  }
+  __syncthreads();
+
+  // ---- 2. faces: one item per (face, field), four lanes per face
+  constexpr int NITEMS = 4 * (G::NXF + G::NYF);
+  static_assert((4 * G::NXF) % 32 == 0, "x/y items must not share a warp");
+  const int lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int base = 0; base < NITEMS; base += kThreads) {
+    const int w = base + threadIdx.x;
+    if (base + (threadIdx.x & ~31) >= NITEMS) break;  // whole warp past the end
+    const int face = w >> 2;
+    const int m = min(w & 3, NV - 1);
+    const int dir = face < G::NXF ? 0 : 1;  // warp-uniform
+    int cb0, stride, gf, gline;
+    if (dir == 0) {
+      const int r = face / (TX + 1), f = face % (TX + 1);
+      cb0 = (G::HY + r) * SX + f;
+      stride = 1;
+      gf = i0 + f;      // global face index along x, 0..nx
+      gline = j0 + r;   // row
+    } else {
+      const int fl = face - G::NXF;
+      const int f = fl / TX, c = fl % TX;
+      cb0 = f * SX + 3 + c;
+      stride = SX;
+      gf = j0 + f;
+      gline = i0 + c;   // column
+    }
+    const bool valid = (w & 3) < NV &&
+                       (dir == 0 ? (gf <= nx && gline < ny) : (gf <= ny && gline < nx));
+    const double* Fl = C + (dir == 0 ? CA::Fx : CA::Fy) * NC;
+    const double* Un = C + (dir == 0 ? CA::u : CA::v) * NC;  // normal velocity
+    const int ca = cb0 + 2 * stride, cbb = cb0 + 3 * stride;
+
+    // Roe average of cells i and i+1 (Sec. 4.4).
+    const double sa = C[CA::s * NC + ca], sb = C[CA::s * NC + cbb];
+    const double den = __dadd_rn(sa, sb);
+    const double ut = __ddiv_rn(__fma_rn(sb, C[CA::u * NC + cbb], __dmul_rn(sa, C[CA::u * NC + ca])), den);
+    const double Ht = __ddiv_rn(__fma_rn(sb, C[CA::H * NC + cbb], __dmul_rn(sa, C[CA::H * NC + ca])), den);
+    double vt = 0.0, qt;
+    if (NDIM == 2) {
+      vt = __ddiv_rn(__fma_rn(sb, C[CA::v * NC + cbb], __dmul_rn(sa, C[CA::v * NC + ca])), den);
+      qt = __fma_rn(vt, vt, __dmul_rn(ut, ut));
+    } else {
+      qt = __dmul_rn(ut, ut);
+    }
+    const double c2 = __dmul_rn(gm1, __dsub_rn(Ht, __dmul_rn(0.5, qt)));
+    if (valid && !(c2 > 0.0)) atomicOr(a.status, 2);
+    const double ct = __dsqrt_rn(c2);
+    const double ic = __ddiv_rn(1.0, ct);
+    const double b1 = __ddiv_rn(gm1, c2);
+    const double b2 = __dmul_rn(0.5, __dmul_rn(b1, qt));
+    const double nt = dir == 0 ? ut : vt;
+    const double nc = __dmul_rn(nt, ic);
+    const double b1u = __dmul_rn(b1, ut), b1v = __dmul_rn(b1, vt);
+    const double hb1 = __dmul_rn(0.5, b1), ntc = __dmul_rn(nt, ct);
+
+    // Left eigenvector (row m of L) and right-eigenvector components (row m
+    // of R, i.e. component m of every column) in the Roe/Toro scaling.
+    double L[4], R[4];
+    {
+      const double am = __dmul_rn(0.5, __dadd_rn(b2, nc));   // acoustic "-" first entry
+      const double ap = __dmul_rn(0.5, __dsub_rn(b2, nc));   // acoustic "+" first entry
+      const double nb1u = -b1u, nb1v = -b1v;
+      const double hm_u = __dmul_rn(0.5, __dsub_rn(nb1u, ic)), hp_u = __dmul_rn(0.5, __dadd_rn(nb1u, ic));
+      if (NDIM == 1) {
+        if (m == 0) { L[0] = am; L[1] = hm_u; L[2] = hb1; }
+        else if (m == 1) { L[0] = __dsub_rn(1.0, b2); L[1] = b1u; L[2] = -b1; }
+        else { L[0] = ap; L[1] = hp_u; L[2] = hb1; }
+        L[3] = 0.0;
+        if (m == 0) { R[0] = 1.0; R[1] = 1.0; R[2] = 1.0; }
+        else if (m == 1) { R[0] = __dsub_rn(ut, ct); R[1] = ut; R[2] = __dadd_rn(ut, ct); }
+        else { R[0] = __dsub_rn(Ht, ntc); R[1] = __dmul_rn(0.5, qt); R[2] = __dadd_rn(Ht, ntc); }
+        R[3] = 0.0;
+      } else {
+        const double hnb1v = __dmul_rn(0.5, nb1v), hnb1u = __dmul_rn(0.5, nb1u);
+        const double hm_v = __dmul_rn(0.5, __dsub_rn(nb1v, ic)), hp_v = __dmul_rn(0.5, __dadd_rn(nb1v, ic));
+        if (m == 0) {
+          L[0] = am; L[1] = dir == 0 ? hm_u : hnb1u; L[2] = dir == 0 ? hnb1v : hm_v; L[3] = hb1;
+        } else if (m == 1) {
+          L[0] = __dsub_rn(1.0, b2); L[1] = b1u; L[2] = b1v; L[3] = -b1;
+        } else if (m == 2) {
+          L[0] = dir == 0 ? -vt : -ut; L[1] = dir == 0 ? 0.0 : 1.0; L[2] = dir == 0 ? 1.0 : 0.0; L[3] = 0.0;
+        } else {
+          L[0] = ap; L[1] = dir == 0 ? hp_u : hnb1u; L[2] = dir == 0 ? hnb1v : hp_v; L[3] = hb1;
+        }
+        if (m == 0) { R[0] = 1.0; R[1] = 1.0; R[2] = 0.0; R[3] = 1.0; }
+        else if (m == 1) {
+          if (dir == 0) { R[0] = __dsub_rn(ut, ct); R[1] = ut; R[2] = 0.0; R[3] = __dadd_rn(ut, ct); }
+          else { R[0] = ut; R[1] = ut; R[2] = 1.0; R[3] = ut; }
+        } else if (m == 2) {
+          if (dir == 0) { R[0] = vt; R[1] = vt; R[2] = 1.0; R[3] = vt; }
+          else { R[0] = __dsub_rn(vt, ct); R[1] = vt; R[2] = 0.0; R[3] = __dadd_rn(vt, ct); }
+        } else {
+          R[0] = __dsub_rn(Ht, ntc); R[1] = __dmul_rn(0.5, qt); R[2] = dir == 0 ? vt : ut;
+          R[3] = __dadd_rn(Ht, ntc);
+        }
+      }
+    }
+
+    // LLF alpha_m: max over the six stencil cells of |lambda_m|.
+    double alpha = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int cj = cb0 + j * stride;
+      const double un = Un[cj], cs = C[CA::c * NC + cj];
+      const double lam = m == 0 ? __dsub_rn(un, cs) : (m == NV - 1 ? __dadd_rn(un, cs) : un);
+      alpha = j == 0 ? dabs(lam) : dmax_nn(alpha, dabs(lam));
+    }
+
+    // Characteristic projection and LLF split of the six stencil cells.
+    double sp[6], sm[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int cj = cb0 + j * stride;
+      double vv = __dmul_rn(L[0], C[(CA::U + 0) * NC + cj]);
+      double gg = __dmul_rn(L[0], Fl[0 * NC + cj]);
+#pragma unroll
+      for (int n = 1; n < NV; ++n) {
+        vv = __fma_rn(L[n], C[(CA::U + n) * NC + cj], vv);
+        gg = __fma_rn(L[n], Fl[n * NC + cj], gg);
+      }
+      sp[j] = __dmul_rn(0.5, __fma_rn(alpha, vv, gg));
+      sm[j] = __dmul_rn(0.5, __fma_rn(-alpha, vv, gg));
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      park[j * kThreads] = sp[j];
+      park[(6 + j) * kThreads] = sm[5 - j];  // the "-" side is the mirror image
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) park[(12 + q) * kThreads] = R[q];
+
+    // Classifier bits of both sides ("-" side = mirror image).
+    // Compiler-level barrier: the parked values must be re-read from shared
+    // memory, not kept live in registers across the classifier.
+    asm volatile("" ::: "memory");
+    unsigned eta_side[2];
+    if (a.mask_mode == kMaskMLP) {
+#pragma unroll 1
+      for (int side = 0; side < 2; ++side) {
+        double st[6], x[6], z[4];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) st[j] = park[(side * 6 + j) * kThreads];
+        normalise6(st, x);
+        eta_side[side] = mlp64(net, x, z);
+      }
+    } else if (a.mask_mode == kMaskGiven) {
+      size_t idx;
+      if (dir == 0) idx = ((size_t)m * ny + gline) * (nx + 1) + gf;
+      else idx = (size_t)NV * ny * (nx + 1) + ((size_t)m * (ny + 1) + gf) * nx + gline;
+      const unsigned b = valid ? a.mask_in[idx] : 0u;
+      eta_side[0] = b & 15u;
+      eta_side[1] = b >> 4;
+    } else {
+      eta_side[0] = eta_side[1] = a.mask_mode == kMaskRough ? 15u : 0u;
+    }
+    asm volatile("" ::: "memory");
+    double spl[6], smir[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      spl[j] = park[j * kThreads];
+      smir[j] = park[(6 + j) * kThreads];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) R[q] = park[(12 + q) * kThreads];
+    const double gp = combine64(a, spl, eta_side[0]);
+    const double gmn = combine64(a, smir, eta_side[1]);
+    const double gh = __dadd_rn(gp, gmn);
+
+    // Back-projection F_n = sum_m R[n][m] gh_m; lane m of the face holds gh_m
+    // and computes component n = m.
+    const int fbase = lane & ~3;
+    double ghm[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ghm[q] = __shfl_sync(0xffffffffu, gh, fbase + q);
+    double Fh = __dmul_rn(R[0], ghm[0]);
+#pragma unroll
+    for (int q = 1; q < NV; ++q) Fh = __fma_rn(R[q], ghm[q], Fh);
+
+    if (valid) {
+      if (dir == 0) {
+        const int r = face / (TX + 1), f = face % (TX + 1);
+        sFx[(m * TY + r) * (TX + 1) + f] = Fh;
+      } else {
+        const int fl = face - G::NXF;
+        sFy[(m * (TY + 1) + fl / TX) * TX + fl % TX] = Fh;
+      }
+      if (a.mask_out) {
+        size_t idx;
+        if (dir == 0) idx = ((size_t)m * ny + gline) * (nx + 1) + gf;
+        else idx = (size_t)NV * ny * (nx + 1) + ((size_t)m * (ny + 1) + gf) * nx + gline;
+        a.mask_out[idx] = (uint8_t)(eta_side[0] | (eta_side[1] << 4));
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 3. conservative difference and (optionally) the RK3 stage update
+  for (int e = threadIdx.x; e < TX * TY; e += kThreads) {
+    const int c = e % TX, r = e / TX;
+    const int gi = i0 + c, gj = j0 + r;
+    if (gi >= nx || gj >= ny) continue;
+    const size_t g = (size_t)gj * nx + gi;
+    const int bc = (G::HY + r) * SX + 3 + c;
+#pragma unroll
+    for (int n = 0; n < NV; ++n) {
+      const double Fp = sFx[(n * TY + r) * (TX + 1) + c + 1];
+      const double Fm = sFx[(n * TY + r) * (TX + 1) + c];
+      double rr = -__ddiv_rn(__dsub_rn(Fp, Fm), a.dx);
+      if (NDIM == 2) {
+        const double Gp = sFy[(n * (TY + 1) + r + 1) * TX + c];
+        const double Gm = sFy[(n * (TY + 1) + r) * TX + c];
+        rr = __dsub_rn(rr, __ddiv_rn(__dsub_rn(Gp, Gm), a.dy));
+      }
+      double val = rr;
+      const double Ucur = C[(CA::U + n) * NC + bc];
+      if (a.stage == 1) {
+        val = __fma_rn(dt, rr, Ucur);
+      } else if (a.stage == 2) {
+        val = __fma_rn(0.75, a.U0[n * plane + g], __dmul_rn(0.25, __fma_rn(dt, rr, Ucur)));
+      } else if (a.stage == 3) {
+        val = __fma_rn(a.third, a.U0[n * plane + g], __dmul_rn(a.two_thirds, __fma_rn(dt, rr, Ucur)));
+      }
+      a.out[n * plane + g] = val;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) classify_fp64_kernel(const __grid_constant__ ClassifyParamsF64 P) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.n) return;
+  double s[6], x[6], z[4];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s[j] = P.X[r * 6 + j];
+  normalise6(s, x);
+  const unsigned eta = mlp64(P.net.p, x, z);
+  P.eta[r] = (uint8_t)eta;
+  if (P.logits) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P.logits[r * 4 + k] = z[k];
+  }
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+// max over cells of |u|+c (and |v|+c): bit patterns of non-negative doubles
+// order like the values, so integer max / atomicMax give the exact maximum.
+template <int NDIM>
+__global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restrict__ U, int nx, int ny,
+                                                         double gamma, unsigned long long* smax,
+                                                         int* status) {
+  const size_t plane = (size_t)nx * ny;
+  const double gm1 = __dsub_rn(gamma, 1.0);
+  unsigned long long mx = 0, my = 0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double rho = U[k];
+    const double E = U[(NDIM == 2 ? 3 : 2) * plane + k];
+    const double u = __ddiv_rn(U[plane + k], rho);
+    double v = 0.0, q;
+    if (NDIM == 2) {
+      v = __ddiv_rn(U[2 * plane + k], rho);
+      q = __fma_rn(v, v, __dmul_rn(u, u));
+    } else {
+      q = __dmul_rn(u, u);
+    }
+    const double p = __dmul_rn(gm1, __dsub_rn(E, __dmul_rn(0.5, __dmul_rn(rho, q))));
+    const double c = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), rho));
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(status, 1);
+    mx = umax64(mx, (unsigned long long)dbits(__dadd_rn(dabs(u), c)));
+    if (NDIM == 2) my = umax64(my, (unsigned long long)dbits(__dadd_rn(dabs(v), c)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = umax64(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = umax64(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  __shared__ unsigned long long wx[8], wy[8];
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wx[warp] = mx;
+    wy[warp] = my;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      mx = umax64(mx, wx[i]);
+      my = umax64(my, wy[i]);
+    }
+    atomicMax(&smax[0], mx);
+    if (NDIM == 2) atomicMax(&smax[1], my);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s) {
+  if (ndim == 2) {
+    using G = Geom<2>;
+    constexpr size_t sm = rhs_smem_bytes<2>();
+    cudaError_t e = cudaFuncSetAttribute(rhs_fp64_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.a.nx + G::TX - 1) / G::TX, (p.a.ny + G::TY - 1) / G::TY);
+    rhs_fp64_kernel<2><<<grid, kThreads, sm, s>>>(p);
+  } else {
+    using G = Geom<1>;
+    constexpr size_t sm = rhs_smem_bytes<1>();
+    cudaError_t e = cudaFuncSetAttribute(rhs_fp64_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.a.nx + G::TX - 1) / G::TX, 1);
+    rhs_fp64_kernel<1><<<grid, kThreads, sm, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s) {
+  if (p.n == 0) return cudaSuccess;
+  const long long blocks = (p.n + 255) / 256;
+  classify_fp64_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
+                              unsigned long long* smax, int* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const size_t cells = (size_t)nx * ny;
+  unsigned blocks = (unsigned)((cells + 255) / 256);
+  if (blocks > 152u * 8u) blocks = 152u * 8u;
+  if (ndim == 2)
+    cfl_reduce_kernel<2><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
+  else
+    cfl_reduce_kernel<1><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
+  return cudaGetLastError();
+}
+
+}  // namespace neno6

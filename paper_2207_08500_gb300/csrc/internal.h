@@ -1,0 +1,63 @@
+// Internal declarations shared by the library's translation units: kernel
+// parameter blocks and launcher entry points.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace neno6 {
+
+// Classifier of Sec. 3.1: widths 6-64-32-16-8-4; parameters packed per layer
+// as W[out][in] row-major followed by b[out] (the weights-file order).
+constexpr int kNetWidths[6] = {6, 64, 32, 16, 8, 4};
+constexpr int kNetParams = 6 * 64 + 64 + 64 * 32 + 32 + 32 * 16 + 16 + 16 * 8 + 8 + 8 * 4 + 4;
+static_assert(kNetParams == 3228, "6-64-32-16-8-4 parameter count");
+
+struct NetF64 {
+  double p[kNetParams];
+};
+
+// Mask modes (public NENO6_MASK_* plus the frozen-mask mode).
+enum MaskMode { kMaskMLP = 0, kMaskSmooth = 1, kMaskRough = 2, kMaskGiven = 3 };
+
+// Arguments of one RHS / RK3-stage launch.
+struct RhsArgs {
+  const double* U;   // state the right-hand side is evaluated on
+  const double* U0;  // state at the start of the RK3 step (stages 2, 3)
+  double* out;       // dU/dt (stage 0) or the next stage state
+  const uint8_t* mask_in;
+  uint8_t* mask_out;
+  int* status;
+  const unsigned long long* smax;  // stage 1: bit patterns of max(|u|+c), max(|v|+c)
+  double* dt_dev;                  // stage 1 writes, stages 2/3 read
+  double* t_dev;                   // stage 1 reads, stage 3 advances
+  double* dt_user;                 // nullable copy of dt for the caller
+  int nx, ny, bcx, bcy;
+  int mask_mode;
+  int stage;  // 0 = dU/dt; 1, 2, 3 = SSP-RK3 stages
+  double dx, dy, gamma, gm1;
+  double cfl, t_end;
+  double third, two_thirds;
+  double cand[4][4];   // candidate coefficients, stencil order
+  double wtab[16][4];  // renormalised weights d_k / sum(kept d) per mask
+};
+
+struct RhsParamsF64 {
+  RhsArgs a;
+  NetF64 net;
+};
+
+struct ClassifyParamsF64 {
+  const double* X;
+  uint8_t* eta;
+  double* logits;
+  long long n;
+  NetF64 net;
+};
+
+cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
+cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s);
+cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
+                              unsigned long long* smax, int* status, cudaStream_t s);
+
+}  // namespace neno6
