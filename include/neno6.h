@@ -168,6 +168,50 @@ int neno6_status(neno6_handle* h, int* device_status, void* stream);
  * NULL; "" when none).  With h == NULL: the last create failure. */
 const char* neno6_last_error(const neno6_handle* h);
 
+/*
+ * neno6_step_noalloc — the SSP-RK3 step of neno6_step, for callers that must
+ * not allocate device memory.  (No counterpart in the paper: an interface
+ * choice of this library.)
+ *
+ * Who needs it: code that runs inside a host application which has reserved
+ * the GPU's memory up front for its own pool, or that runs under a fixed
+ * device-memory budget, cannot call cudaMalloc mid-run (the call may fail or
+ * take memory the owner accounted for), and a cudaMalloc / cudaFree also
+ * synchronises the device, stalling the other streams of a latency-critical
+ * loop.  neno6_create allocates (weights, status word, and neno6_step's
+ * stage buffers on first use); this entry point needs no handle and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Scratch: one file-scope static device array holding two stage states of at
+ * most NENO6_NOALLOC_MAX_STATE_ELEMS float64 values each (4 MiB each) plus a
+ * few words; every GPU that loads the library holds it (8 MiB) until the
+ * process exits.  Every call shares it and it keeps the previous call's
+ * contents; the call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.
+ *
+ *   cfg          host pointer: grid and scheme (precision must be NENO6_FP64);
+ *                nv * nx * ny must not exceed NENO6_NOALLOC_MAX_STATE_ELEMS.
+ *   net_params   host pointer: the 3228 classifier parameters in the weights
+ *                file's order (per layer W[out][in] then b[out]); n_params
+ *                must be 3228.
+ *   U            [nv][ny][nx] float64 device state, advanced in place.
+ *   cfl, t_end   as in neno6_step.
+ *   t_dev        nullable device float64 time, advanced by dt; NULL: the step
+ *                starts from t = 0.
+ *   dt_dev       nullable device float64 receiving dt.
+ *   status_dev   nullable device int; NENO6_STATUS_* bits are OR-ed into it
+ *                (NULL: they are dropped).
+ * Returns NENO6_OK or ARG, SHAPE (state larger than the static scratch),
+ * ALIGN, WEIGHTS (n_params), UNSUPPORTED, CUDA; no message is recorded.
+ */
+#define NENO6_NOALLOC_MAX_STATE_ELEMS (1u << 19)
+int neno6_step_noalloc(const neno6_config* cfg, const double* net_params, int64_t n_params,
+                       double* U, double cfl, double t_end, double* t_dev, double* dt_dev,
+                       int* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

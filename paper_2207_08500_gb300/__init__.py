@@ -25,7 +25,7 @@ MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
-           "neno6_classify", "neno6_status", "neno6_last_error")
+           "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc")
 
 
 class Neno6Error(RuntimeError):
@@ -64,6 +64,8 @@ def load_library(path=LIB_PATH):
     lib.neno6_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     lib.neno6_last_error.argtypes = [vp]
     lib.neno6_last_error.restype = ctypes.c_char_p
+    lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
+                                       ctypes.c_double, dp, dp, vp, vp]
     _lib = lib
     return lib
 

@@ -26,6 +26,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
 SOURCES = {
     "api.cu": [],
     "fp64.cu": ["-fmad=false"],
+    "noalloc.cu": [],
 }
 
 
