@@ -27,6 +27,7 @@ SOURCES = {
     "api.cu": [],
     "fp64.cu": ["-fmad=false"],
     "noalloc.cu": [],
+    "mixed.cu": [],
 }
 
 

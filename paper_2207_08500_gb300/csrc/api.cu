@@ -27,6 +27,7 @@ struct neno6_handle {
   double* d_dt = nullptr;     // dt of the current step
   double* d_t = nullptr;      // internal time (neno6_step with t_dev == NULL)
   double* d_stage = nullptr;  // two RK3 stage states (lazily allocated)
+  uint8_t* d_net_image = nullptr;  // tensor-core classifier image (mixed precision)
   size_t state_elems = 0;
   RhsParamsF64 rhs_params;        // launch parameter blocks (copied at launch)
   ClassifyParamsF64 cls_params;
@@ -189,8 +190,6 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
     return fail(nullptr, NENO6_ERR_ARG, "bad mask_mode");
   if (c.precision != NENO6_FP64 && c.precision != NENO6_MIXED_BF16 && c.precision != NENO6_MIXED_FP16)
     return fail(nullptr, NENO6_ERR_ARG, "bad precision");
-  if (c.precision != NENO6_FP64)
-    return fail(nullptr, NENO6_ERR_UNSUPPORTED, "mixed precision is not available in this build");
 
   neno6_handle* h = new (std::nothrow) neno6_handle();
   if (!h) return fail(nullptr, NENO6_ERR_ARG, "out of host memory");
@@ -211,6 +210,12 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
   if (e == cudaSuccess) e = cudaMalloc(&h->d_t, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_t, 0, sizeof(double));
+  if (e == cudaSuccess && c.precision != NENO6_FP64) {
+    std::vector<uint8_t> img(kNetImageBytes);
+    build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
+    e = cudaMalloc(&h->d_net_image, kNetImageBytes);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_net_image, img.data(), kNetImageBytes, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     std::string m = std::string("device setup: ") + cudaGetErrorString(e);
@@ -229,6 +234,7 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_dt);
   cudaFree(h->d_t);
   cudaFree(h->d_stage);
+  cudaFree(h->d_net_image);
   delete h;
   return NENO6_OK;
 }
@@ -245,6 +251,7 @@ int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mas
               uint8_t* mask_out, void* stream) {
   if (!h) return NENO6_ERR_ARG;
   if (!U || !dUdt) return fail(h, NENO6_ERR_ARG, "rhs: null state pointer");
+  if (h->cfg.precision != NENO6_FP64) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs: mixed precision not built yet");
   if (!aligned(U, 16) || !aligned(dUdt, 16)) return fail(h, NENO6_ERR_ALIGN, "rhs: U/dUdt must be 16-byte aligned");
   if ((const void*)U == (const void*)dUdt) return fail(h, NENO6_ERR_ARG, "rhs: dUdt must not alias U");
   RhsParamsF64& p = h->rhs_params;
@@ -265,6 +272,7 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
                void* stream) {
   if (!h) return NENO6_ERR_ARG;
   if (!U) return fail(h, NENO6_ERR_ARG, "step: null state pointer");
+  if (h->cfg.precision != NENO6_FP64) return fail(h, NENO6_ERR_UNSUPPORTED, "step: mixed precision not built yet");
   if (!aligned(U, 16)) return fail(h, NENO6_ERR_ALIGN, "step: U must be 16-byte aligned");
   if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step: need cfl > 0, t_end >= 0");
   cudaStream_t s = (cudaStream_t)stream;
@@ -309,6 +317,12 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
   if (n == 0) return NENO6_OK;
   if (!X || !eta_out) return fail(h, NENO6_ERR_ARG, "classify: null pointer");
   if (!aligned(X, 8) || (logits && !aligned(logits, 8))) return fail(h, NENO6_ERR_ALIGN, "classify: misaligned");
+  if (h->cfg.precision != NENO6_FP64) {
+    cudaError_t e = launch_classify_mixed(X, n, eta_out, logits, h->d_net_image,
+                                          h->cfg.precision == NENO6_MIXED_BF16, h->d_status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "classify launch");
+    return NENO6_OK;
+  }
   ClassifyParamsF64& p = h->cls_params;
   p.X = X;
   p.eta = eta_out;

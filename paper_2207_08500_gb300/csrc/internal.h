@@ -55,7 +55,23 @@ struct ClassifyParamsF64 {
   NetF64 net;
 };
 
+// Tensor-core image of the classifier (mixed precision): 16-bit B operands
+// W_l[out][in] in the K-major canonical layout (N and K padded to multiples
+// of 16), then the FP32 biases at columns 0 / 64 / 96 / 112 / 128.
+constexpr int kNetImageB1 = 0;                         // 64 x 16
+constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;  // 32 x 64
+constexpr int kNetImageB3 = kNetImageB2 + 32 * 64 * 2;  // 16 x 32
+constexpr int kNetImageB4 = kNetImageB3 + 16 * 32 * 2;  // 16 x 16 (8 real rows)
+constexpr int kNetImageB5 = kNetImageB4 + 16 * 16 * 2;  // 16 x 16 (4 x 8 real)
+constexpr int kNetImageBias = kNetImageB5 + 16 * 16 * 2;
+constexpr int kNetImageBytes = kNetImageBias + 144 * 4;
+static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");
+
+void build_net_image(const NetF64& net, bool bf16, uint8_t* img);
+
 cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
+cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
+                                  const uint8_t* net_image, bool bf16, int* status, cudaStream_t s);
 cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s);
 cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
                               unsigned long long* smax, int* status, cudaStream_t s);
