@@ -5,8 +5,12 @@ reduction and three fused right-hand-side evaluations (the hot path: ghost
 cells, Roe characteristic projection, LLF split, classifier, renormalised
 combination, back-projection, conservative difference, stage update).
 
-Default workload (N=1): 2D Euler, 2048 x 2048 periodic grid, seeded
-four-quadrant states with a sinusoidal density perturbation, FP64 path.
+Default workload (N=1): 2D Euler, 4096 x 4096 periodic grid, seeded
+four-quadrant states with a sinusoidal density perturbation, mixed-precision
+path (bf16 tensor-core classifier, FP32 reconstruction, FP64 Roe
+eigenvectors / back-projection / difference / RK3).  Beside it the FP64 GPU
+path on the same state (speed, mask flip rate, L1/Linf error of dU/dt and of
+the state after one step).  `--precision fp64 --n 2048` gives the FP64 line.
 Metric: Mcell-updates/s (cells x steps / s), higher is better.
 
 `--impl reference` times the FP64 CPU oracle on the same workload's
@@ -61,6 +65,18 @@ def flops_per_cell_rhs(ndim=2):
     per_face = roe + eig + alpha + nv * per_field + nv * (1 + 2 * (nv - 1))
     per_cell = 25 + nv * (5 if ndim == 2 else 2)
     return ndim * per_face + per_cell
+
+
+def fp64_flops_per_cell_rhs_mixed(ndim=2):
+    """Algorithmic binary64 flops of one cell's RHS in the mixed path, i.e.
+    the parts kept in FP64: per cell the Roe inputs and fluxes (1/rho, u, v,
+    q, p, H, sqrt(rho), one flux per direction), per face the Roe average and
+    eigenvectors (29 + 15) and the back-projection (4 x 7), per cell the
+    difference and the RK3 stage (nv x 9)."""
+    nv = 4 if ndim == 2 else 3
+    per_cell = 1 + 2 + 3 + 4 + 2 + 1 + ndim * 4
+    per_face = 29 + 15 + nv * (1 + 2 * (nv - 1))
+    return per_cell + ndim * per_face + nv * 9
 
 
 # ----------------------------------------------------------------- clocks
@@ -128,7 +144,8 @@ def run_ours(args, rank, world):
     n = args.n
     cfl = 0.4
     weights = args.weights
-    solver = neno6.Neno6(ndim=2, nx=n, ny=n, bc=("periodic", "periodic"), precision="fp64",
+    prec = args.precision
+    solver = neno6.Neno6(ndim=2, nx=n, ny=n, bc=("periodic", "periodic"), precision=prec,
                          weights=weights)
     U0 = synth.quadrants_2d(n, n)  # seeded, identical on every rank (weak scaling)
     U = torch.from_numpy(U0).to(dev)
@@ -191,6 +208,44 @@ def run_ours(args, rank, world):
     e2e_ms = f0.elapsed_time(f1)
     status = solver.status()
 
+    # mixed precision against the FP64 GPU path (itself bit-exact with the
+    # oracle) on the same state: decisions, dU/dt, and one RK3 step
+    compare = None
+    if prec != "fp64" and not args.no_compare:
+        ref = neno6.Neno6(ndim=2, nx=n, ny=n, bc=("periodic", "periodic"), precision="fp64",
+                          weights=weights)
+        S0 = torch.from_numpy(U0).to(dev)
+        d64, m64 = ref.rhs(S0, want_mask=True)
+        dmx, mmx = solver.rhs(S0, want_mask=True)
+        flips = int(np.unpackbits(torch.bitwise_xor(m64, mmx).cpu().numpy()).sum())
+        a, b = dmx.double(), d64
+        rhs_l1 = ((a - b).abs().sum() / b.abs().sum()).item()
+        rhs_linf = ((a - b).abs().max() / b.abs().max()).item()
+        del d64, dmx
+        A, B = S0.clone(), S0.clone()
+        ta = torch.zeros(1, dtype=torch.float64, device=dev)
+        tb = torch.zeros(1, dtype=torch.float64, device=dev)
+        ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev64[0].record(stream)
+        ref.step(A, cfl, t=ta)
+        ev64[1].record(stream)
+        solver.step(B, cfl, t=tb)
+        torch.cuda.synchronize()
+        fp64_ms = ev64[0].elapsed_time(ev64[1])
+        st_l1 = ((B - A).abs().sum() / A.abs().sum()).item()
+        st_linf = ((B - A).abs().max() / A.abs().max()).item()
+        compare = {
+            "fp64_gpu_value": round(n * n / (fp64_ms * 1e-3) / 1e6, 4), "unit": UNIT,
+            "fp64_gpu_ms_per_step": round(fp64_ms, 3),
+            "mask_flip_rate": flips / (8.0 * m64.numel()),
+            "rhs_rel_l1": rhs_l1, "rhs_rel_linf": rhs_linf,
+            "state_rel_l1_one_step": st_l1, "state_rel_linf_one_step": st_linf,
+            "reference": "FP64 GPU path (bit-exact with the FP64 oracle in the parity tests)",
+            "guard_tau": solver.config.guard_tau,
+        }
+        ref.close()
+        del A, B, S0, m64, mmx
+
     # max over ranks
     vals = torch.tensor([ms, e2e_ms, rhs_avg], dtype=torch.float64, device=dev)
     if world > 1:
@@ -200,20 +255,31 @@ def run_ours(args, rank, world):
     cells = n * n
     value = cells * args.steps * world / (ms * 1e-3) / 1e6
     e2e_value = cells * e2e_steps * world / (e2e_ms * 1e-3) / 1e6
-    fl = flops_per_cell_rhs(2) * cells
+    if prec == "fp64":
+        fl = flops_per_cell_rhs(2) * cells
+        kname = "rhs_fp64_kernel"
+        fl_note = "all binary64 flops of the scheme (bench.flops_per_cell_rhs)"
+        launches_per_step = 4
+    else:
+        fl = fp64_flops_per_cell_rhs_mixed(2) * cells
+        kname = "faces_mixed_kernel + diff_mixed_kernel (one RHS)"
+        fl_note = ("binary64 flops of the parts the mixed path keeps in FP64 "
+                   "(bench.fp64_flops_per_cell_rhs_mixed); FP32 and tensor-core work not counted")
+        launches_per_step = 8
     achieved = fl / (rhs_avg * 1e-3) / 1e12
     peak = fp64_peak_tflops()
     state_bytes = U.numel() * 8
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "%s+f32+f64" % prec,
         "data": "synthetic (seeded four-quadrant Euler states, trained frozen classifier)",
-        "config": {"workload": "2D Euler 2048x2048 periodic, FP64 NENO6 RHS, SSP-RK3 (CFL 0.4)",
-                   "nx": n, "ny": n, "precision": "fp64", "step": "one SSP-RK3 step = 3 RHS",
+        "config": {"workload": workload_name(n, prec),
+                   "nx": n, "ny": n, "precision": prec, "step": "one SSP-RK3 step = 3 RHS",
                    "l2": "inputs larger than L2 (state %d MB)" % (state_bytes >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "alu", "kernel": "rhs_fp64_kernel",
+        "roofline": {"bound": "alu", "kernel": kname, "flops_counted": fl_note,
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_source": "FP64 pipe: measured DFMA rate per SM per clock x 152 SMs x "
@@ -221,7 +287,8 @@ def run_ours(args, rank, world):
                      "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3)},
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
+        "vs_fp64_gpu": compare,
         "clocks": clock_info,
         "device_status": status,
     }
@@ -252,6 +319,11 @@ def oracle_timing(crop=64, reps=1):
     return crop * crop * reps / dt / 1e6, dt
 
 
+def workload_name(n, prec):
+    return "2D Euler %dx%d periodic, %s NENO6 RHS, SSP-RK3 (CFL 0.4)" % (
+        n, n, "FP64" if prec == "fp64" else "mixed-precision (%s classifier)" % prec)
+
+
 def run_reference(args):
     oracle_timing(16, 1)  # build + warm the oracle library
     for _ in range(args.warmup):
@@ -261,14 +333,14 @@ def run_reference(args):
         oracle_timing(args.ref_crop, 1)
     dt = time.perf_counter() - t0
     value = args.ref_crop ** 2 * args.steps / dt / 1e6
-    sample = "one SSP-RK3 step of a %dx%d periodic crop of the 2048^2 workload per step" % (
-        args.ref_crop, args.ref_crop)
+    sample = ("one FP64 SSP-RK3 step of the oracle on a %dx%d periodic crop of the %d^2 "
+              "workload per step" % (args.ref_crop, args.ref_crop, args.n))
     return {
         "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1, "impl": "reference",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "2D Euler 2048x2048 periodic, FP64 NENO6 RHS, "
-                                                    "SSP-RK3 (CFL 0.4)", "sample": sample},
+        "data": "synthetic", "config": {"workload": workload_name(args.n, args.precision),
+                                        "sample": sample},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -276,18 +348,43 @@ def run_reference(args):
     }
 
 
+def run_rhs_only(args):
+    """`--rhs-only`: warm-up + `--steps` plain RHS evaluations (a case for
+    profilers); prints one line, no timing."""
+    import torch
+    import paper_2207_08500_gb300 as neno6
+    import synth
+    n = args.n
+    g = neno6.Neno6(ndim=2, nx=n, ny=n, precision=args.precision, weights=args.weights)
+    U = torch.from_numpy(synth.quadrants_2d(n, n)).cuda()
+    d = torch.empty_like(U)
+    for _ in range(args.warmup + args.steps):
+        g.rhs(U, out=d)
+    torch.cuda.synchronize()
+    print(json.dumps({"rhs_only": True, "n": n, "precision": args.precision,
+                      "launches": args.warmup + args.steps, "status": g.status()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--precision", choices=["fp64", "bf16", "fp16"], default="bf16")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--rhs-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--cpu-crop", type=int, default=96)
     args = ap.parse_args()
+    if args.n is None:
+        args.n = 2048 if args.precision == "fp64" else 4096
 
+    if args.rhs_only:
+        run_rhs_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -54,8 +54,10 @@ extern "C" {
 
 /* neno6_config.precision */
 #define NENO6_FP64 0        /* everything in binary64 (bit-exact masks)    */
-#define NENO6_MIXED_BF16 1  /* MLP in bf16 on tensor cores, see below      */
-#define NENO6_MIXED_FP16 2  /* MLP in fp16 on tensor cores                 */
+#define NENO6_MIXED_BF16 1  /* classifier in bf16 on tensor cores, FP32
+                               reconstruction, FP64 Roe eigenvectors,
+                               back-projection, difference and RK3         */
+#define NENO6_MIXED_FP16 2  /* same with fp16 classifier operands          */
 
 /* neno6_config.bc[axis] */
 #define NENO6_BC_PERIODIC 0
@@ -79,6 +81,8 @@ typedef struct neno6_config {
   int precision;      /* NENO6_FP64 | NENO6_MIXED_BF16 | NENO6_MIXED_FP16  */
   int linear_weights; /* NENO6_W_*                                         */
   int mask_mode;      /* NENO6_MASK_*                                      */
+  double guard_tau;   /* mixed precision: a row whose |logit_k| < guard_tau
+                         for some k is re-evaluated in FP32 (0 = off)       */
 } neno6_config;
 
 typedef struct neno6_handle neno6_handle;

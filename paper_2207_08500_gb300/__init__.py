@@ -22,6 +22,8 @@ PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}
 BC = {"periodic": 0, "transmissive": 1}
 LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
 MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
+# logit band re-evaluated in FP32 by the mixed-precision path
+DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 0.5, "fp16": 0.1}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
@@ -38,7 +40,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("bc", ctypes.c_int * 2), ("precision", ctypes.c_int),
-                ("linear_weights", ctypes.c_int), ("mask_mode", ctypes.c_int)]
+                ("linear_weights", ctypes.c_int), ("mask_mode", ctypes.c_int),
+                ("guard_tau", ctypes.c_double)]
 
 
 _lib = None
@@ -87,7 +90,7 @@ class Neno6:
 
     def __init__(self, ndim=2, nx=64, ny=64, dx=None, dy=None, gamma=1.4,
                  bc=("periodic", "periodic"), precision="fp64", linear_weights="paper",
-                 mask_mode="mlp", weights=DEFAULT_WEIGHTS):
+                 mask_mode="mlp", weights=DEFAULT_WEIGHTS, guard_tau=None):
         if not torch.cuda.is_available():
             raise RuntimeError("NENO6 needs a CUDA device; there is no CPU fallback")
         lib = load_library()
@@ -104,6 +107,9 @@ class Neno6:
         c.precision = PRECISION[precision]
         c.linear_weights = LINEAR_WEIGHTS[linear_weights]
         c.mask_mode = MASK_MODE[mask_mode]
+        if guard_tau is None:
+            guard_tau = DEFAULT_GUARD_TAU.get(precision, 0.0)
+        c.guard_tau = float(guard_tau)
         self.config = c
         self.weights = weights
         h = ctypes.c_void_p()

@@ -28,6 +28,7 @@ SOURCES = {
     "fp64.cu": ["-fmad=false"],
     "noalloc.cu": [],
     "mixed.cu": [],
+    "mixed_rhs.cu": [],
 }
 
 

@@ -28,6 +28,10 @@ struct neno6_handle {
   double* d_t = nullptr;      // internal time (neno6_step with t_dev == NULL)
   double* d_stage = nullptr;  // two RK3 stage states (lazily allocated)
   uint8_t* d_net_image = nullptr;  // tensor-core classifier image (mixed precision)
+  float* d_guard_w = nullptr;      // FP32 transposed parameters (guard band)
+  double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
+  unsigned long long* d_guard_count = nullptr;
+  FacesMixedArgs faces_args;
   size_t state_elems = 0;
   RhsParamsF64 rhs_params;        // launch parameter blocks (copied at launch)
   ClassifyParamsF64 cls_params;
@@ -166,6 +170,72 @@ void fill_rhs_args(const neno6_handle* h, RhsArgs& a) {
   std::memcpy(a.wtab, h->wtab, sizeof a.wtab);
 }
 
+size_t face_elems(const neno6_handle* h) {
+  const size_t nx = h->cfg.nx, ny = h->cfg.ny, nv = h->nv;
+  return nv * ny * (nx + 1) + (h->cfg.ndim == 2 ? nv * (ny + 1) * nx : 0);
+}
+
+int ensure_faces(neno6_handle* h) {
+  if (h->d_faces) return NENO6_OK;
+  cudaError_t e = cudaMalloc(&h->d_faces, face_elems(h) * sizeof(double));
+  if (e != cudaSuccess) {
+    h->d_faces = nullptr;
+    return cuda_fail(h, e, "face-flux buffers");
+  }
+  return NENO6_OK;
+}
+
+// One mixed-precision RHS evaluation of U; stage 0 writes dU/dt to out,
+// stages 1..3 the RK3 stage state (dt from h->d_dt).
+int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, int stage, uint8_t* mask_out,
+              double* t_dev, cudaStream_t s) {
+  int rc = ensure_faces(h);
+  if (rc != NENO6_OK) return rc;
+  FacesMixedArgs& a = h->faces_args;
+  std::memset(&a, 0, sizeof a);
+  a.U = U;
+  a.Fx = h->d_faces;
+  a.Fy = h->d_faces + (size_t)h->nv * h->cfg.ny * (h->cfg.nx + 1);
+  a.mask_out = mask_out;
+  a.status = h->d_status;
+  a.net_image = h->d_net_image;
+  a.guard_w = h->d_guard_w;
+  a.guard_count = h->d_guard_count;
+  a.nx = h->cfg.nx;
+  a.ny = h->cfg.ny;
+  a.bcx = h->cfg.bc[0];
+  a.bcy = h->cfg.bc[1];
+  a.mask_mode = h->cfg.mask_mode;
+  a.bf16 = h->cfg.precision == NENO6_MIXED_BF16;
+  a.guard_tau = (float)h->cfg.guard_tau;
+  a.gamma = h->cfg.gamma;
+  a.gm1 = h->cfg.gamma - 1.0;
+  for (int k = 0; k < 4; ++k)
+    for (int l = 0; l < 4; ++l) a.cand[k][l] = (float)h->cand[k][l];
+  for (int e = 0; e < 16; ++e)
+    for (int k = 0; k < 4; ++k) a.wtab[e][k] = (float)h->wtab[e][k];
+  cudaError_t e = launch_faces_mixed(h->cfg.ndim, a, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mixed face kernel");
+  DiffArgs d;
+  d.Fx = a.Fx;
+  d.Fy = a.Fy;
+  d.U = U;
+  d.U0 = U0;
+  d.out = out;
+  d.dt_dev = h->d_dt;
+  d.t_dev = t_dev;
+  d.nx = h->cfg.nx;
+  d.ny = h->cfg.ny;
+  d.stage = stage;
+  d.inv_dx = 1.0 / h->cfg.dx;
+  d.inv_dy = 1.0 / h->cfg.dy;
+  d.third = 1.0 / 3.0;
+  d.two_thirds = 2.0 / 3.0;
+  e = launch_diff_mixed(h->cfg.ndim, d, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mixed difference kernel");
+  return NENO6_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -215,6 +285,13 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
     build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
     e = cudaMalloc(&h->d_net_image, kNetImageBytes);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_net_image, img.data(), kNetImageBytes, cudaMemcpyHostToDevice);
+    std::vector<float> gimg(kNetParams);
+    build_guard_image(h->net, gimg.data());
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_guard_w, kNetParams * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->d_guard_w, gimg.data(), kNetParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_guard_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(h->d_guard_count, 0, sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -235,6 +312,9 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_t);
   cudaFree(h->d_stage);
   cudaFree(h->d_net_image);
+  cudaFree(h->d_guard_w);
+  cudaFree(h->d_faces);
+  cudaFree(h->d_guard_count);
   delete h;
   return NENO6_OK;
 }
@@ -251,7 +331,12 @@ int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mas
               uint8_t* mask_out, void* stream) {
   if (!h) return NENO6_ERR_ARG;
   if (!U || !dUdt) return fail(h, NENO6_ERR_ARG, "rhs: null state pointer");
-  if (h->cfg.precision != NENO6_FP64) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs: mixed precision not built yet");
+  if (h->cfg.precision != NENO6_FP64) {
+    if (mask_in) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs: frozen masks need the FP64 path");
+    if (!aligned(U, 16) || !aligned(dUdt, 16)) return fail(h, NENO6_ERR_ALIGN, "rhs: U/dUdt must be 16-byte aligned");
+    if ((const void*)U == (const void*)dUdt) return fail(h, NENO6_ERR_ARG, "rhs: dUdt must not alias U");
+    return mixed_rhs(h, U, U, dUdt, 0, mask_out, h->d_t, (cudaStream_t)stream);
+  }
   if (!aligned(U, 16) || !aligned(dUdt, 16)) return fail(h, NENO6_ERR_ALIGN, "rhs: U/dUdt must be 16-byte aligned");
   if ((const void*)U == (const void*)dUdt) return fail(h, NENO6_ERR_ARG, "rhs: dUdt must not alias U");
   RhsParamsF64& p = h->rhs_params;
@@ -272,7 +357,7 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
                void* stream) {
   if (!h) return NENO6_ERR_ARG;
   if (!U) return fail(h, NENO6_ERR_ARG, "step: null state pointer");
-  if (h->cfg.precision != NENO6_FP64) return fail(h, NENO6_ERR_UNSUPPORTED, "step: mixed precision not built yet");
+
   if (!aligned(U, 16)) return fail(h, NENO6_ERR_ALIGN, "step: U must be 16-byte aligned");
   if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step: need cfl > 0, t_end >= 0");
   cudaStream_t s = (cudaStream_t)stream;
@@ -288,6 +373,18 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
   cudaError_t e = launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
                                     h->d_status, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step: cfl reduction");
+  if (h->cfg.precision != NENO6_FP64) {
+    double* tp = t_dev ? t_dev : h->d_t;
+    e = launch_dt(h->d_smax, h->cfg.ndim, h->cfg.dx, h->cfg.dy, cfl, t_end, tp, h->d_dt, dt_dev, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step: dt");
+    const double* in[3] = {U, S1, S2};
+    double* outp[3] = {S1, S2, U};
+    for (int st = 1; st <= 3; ++st) {
+      int rc = mixed_rhs(h, in[st - 1], U, outp[st - 1], st, nullptr, tp, s);
+      if (rc != NENO6_OK) return rc;
+    }
+    return NENO6_OK;
+  }
   RhsParamsF64& p = h->rhs_params;
   fill_rhs_args(h, p.a);
   p.a.smax = h->d_smax;

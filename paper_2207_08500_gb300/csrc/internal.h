@@ -68,6 +68,47 @@ constexpr int kNetImageBytes = kNetImageBias + 144 * 4;
 static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");
 
 void build_net_image(const NetF64& net, bool bf16, uint8_t* img);
+// FP32 parameters with every W transposed to [in][out] (guard re-evaluation).
+void build_guard_image(const NetF64& net, float* img);
+
+// Mixed-precision face kernel arguments.
+struct FacesMixedArgs {
+  const double* U;
+  double* Fx;  // [nv][ny][nx+1] x-face fluxes
+  double* Fy;  // [nv][ny+1][nx] y-face fluxes
+  uint8_t* mask_out;
+  int* status;
+  const uint8_t* net_image;  // tensor-core image
+  const float* guard_w;      // FP32 transposed parameters
+  unsigned long long* guard_count;
+  int nx, ny, bcx, bcy;
+  int mask_mode;
+  int bf16;
+  float guard_tau;
+  double gamma, gm1;
+  float cand[4][4];
+  float wtab[16][4];
+  // filled by the launcher
+  long long nblk_x, nblk_y;
+  int bxf, byc;
+};
+
+struct DiffArgs {
+  const double* Fx;
+  const double* Fy;
+  const double* U;   // stage input
+  const double* U0;  // step start
+  double* out;
+  const double* dt_dev;
+  double* t_dev;
+  int nx, ny, stage;
+  double inv_dx, inv_dy, third, two_thirds;
+};
+
+cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s);
+cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s);
+cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, double dy, double cfl, double t_end,
+                      const double* t_dev, double* dt_dev, double* dt_user, cudaStream_t s);
 
 cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,

@@ -19,125 +19,14 @@
 #include <cstring>
 
 #include "internal.h"
+#include "mlp_tc.cuh"
 #include "tc.cuh"
 
 namespace neno6 {
 namespace {
 
 using namespace tc;
-
-constexpr int kMlpThreads = 128;
-constexpr int kBufXBytes = 128 * 64 * 2;  // A2 (K = 64) / A4
-constexpr int kBufYBytes = 128 * 32 * 2;  // A1 / A3 (K = 32) / A5
-
-__device__ __forceinline__ uint32_t pack2(float a, float b, bool bf16) {
-  if (bf16) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&v);
-  }
-  __half2 v = __floats2half2_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// Store 8 consecutive K values (one core-matrix row) of row `row`.
-__device__ __forceinline__ void st_row8(uint8_t* base, int row, int k0, int K, uint32_t a, uint32_t b,
-                                        uint32_t c, uint32_t d) {
-  const uint32_t addr = smem_u32(base + kmajor_offset(row, k0, K));
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-               : "memory");
-}
-
-struct MlpCtx {
-  const uint8_t* net;  // shared-memory image (kNetImage* layout)
-  uint8_t* bufX;
-  uint8_t* bufY;
-  uint64_t* bar;
-  uint32_t tmem;
-  uint32_t phase;
-  bool bf16;
-};
-
-// Issue one layer (thread 0): ksteps MMAs of K = 16 into TMEM column `col`.
-__device__ __forceinline__ void issue_layer(const MlpCtx& c, const uint8_t* A, int K, int B_off, int N,
-                                            int col) {
-  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-  const uint32_t a0 = smem_u32(A), b0 = smem_u32(c.net + B_off);
-  const uint32_t idesc = idesc_f16(128, N, c.bf16);
-  tc_fence_after();
-  for (int ks = 0; ks < K / 16; ++ks)
-    mma_f16(c.tmem + (uint32_t)col, smem_desc(a0 + 256u * ks, 128u, sbo),
-            smem_desc(b0 + 256u * ks, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
-  mma_commit(c.bar);
-}
-
-// Wait for the layer's MMAs; false on timeout (uniform across the CTA).
-__device__ __forceinline__ bool wait_layer(MlpCtx& c) {
-  const bool ok = mbar_wait(c.bar, c.phase);
-  c.phase ^= 1u;
-  tc_fence_after();
-  return __syncthreads_and(ok ? 1 : 0) != 0;
-}
-
-// Epilogue of a hidden layer: acc(row) + bias -> ReLU -> 16-bit -> next A.
-template <int N>
-__device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bias_off, uint8_t* Anext) {
-  const int t = threadIdx.x;
-  const uint32_t lane = (uint32_t)(t & ~31) << 16;
-  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias) + bias_off;
-#pragma unroll
-  for (int c16 = 0; c16 < N / 16; ++c16) {
-    uint32_t r[16];
-    tmem_ld16(c.tmem + lane + (uint32_t)(col + 16 * c16), r);
-    tmem_ld_wait();
-    uint32_t p[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float a = fmaxf(__uint_as_float(r[2 * i]) + bias[16 * c16 + 2 * i], 0.0f);
-      const float b = fmaxf(__uint_as_float(r[2 * i + 1]) + bias[16 * c16 + 2 * i + 1], 0.0f);
-      p[i] = pack2(a, b, c.bf16);
-    }
-    st_row8(Anext, t, 16 * c16, N, p[0], p[1], p[2], p[3]);
-    st_row8(Anext, t, 16 * c16 + 8, N, p[4], p[5], p[6], p[7]);
-  }
-  tc_fence_before();
-  fence_async_smem();
-  __syncthreads();
-}
-
-// Layers 1..5 for the 128 rows whose layer-1 inputs are in bufY (K = 16).
-// Returns false on an MMA timeout.
-__device__ bool mlp_tc(MlpCtx& c, float z[4]) {
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB1, 64, 0);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<64>(c, 0, 0, c.bufX);
-  if (threadIdx.x == 0) issue_layer(c, c.bufX, 64, kNetImageB2, 32, 64);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<32>(c, 64, 64, c.bufY);
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 32, kNetImageB3, 16, 96);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<16>(c, 96, 96, c.bufX);
-  if (threadIdx.x == 0) issue_layer(c, c.bufX, 16, kNetImageB4, 16, 112);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<16>(c, 112, 112, c.bufY);
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB5, 16, 0);
-  if (!wait_layer(c)) return false;
-  const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
-  uint32_t r[16];
-  tmem_ld16(c.tmem + lane, r);
-  tmem_ld_wait();
-  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias) + 128;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = __uint_as_float(r[k]) + bias[k];
-  tc_fence_before();
-  return true;
-}
-
-// Copy the classifier image (16-byte chunks) into shared memory.
-__device__ __forceinline__ void load_net_image(uint8_t* dst, const uint8_t* __restrict__ src) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  for (int i = threadIdx.x; i < kNetImageBytes / 16; i += blockDim.x) d[i] = s[i];
-}
+using namespace tcmlp;
 
 // Batched classifier (neno6_classify, mixed precision): persistent CTAs of
 // 128 threads, one 128-row tile per iteration.  Normalisation (Eq.

@@ -1,0 +1,483 @@
+// Mixed-precision NENO6 right-hand side (arXiv 2207.08500, Sec. 4.4 and
+// Algorithm 2): every face flux is computed exactly once by a face kernel
+// and written to face-flux arrays; a memory-bound FP64 kernel then forms the
+// conservative difference and the SSP-RK3 stage update.
+//
+// Precision split (GB300: the FP64 pipe is ~1/65 of the FP32 pipe, so the
+// FP64 work is kept to what the method's conditioning needs):
+//   FP64  per-cell Roe inputs (sqrt(rho), u, v, H) and physical fluxes,
+//         Roe average and eigenvectors (Sec. 4.4), back-projection, the
+//         conservative difference (Eq. (approximateEq)), RK3 accumulation;
+//   FP32  LLF alpha, characteristic projection and split, normalisation
+//         (Eq. (normalizainput)), candidates, renormalised combination;
+//   16-bit tensor cores + FP32 accumulation: the classifier (Sec. 3.1), with
+//         rows whose logits fall within +-guard_tau of 0 re-evaluated in FP32
+//         on the CUDA cores.
+//
+// Face kernel: persistent CTAs of one warpgroup (up to four per SM, each with
+// 128 TMEM columns).  A block is 64 faces — 64 consecutive x faces of one
+// row, or 16 columns x 4 consecutive y faces.  Per block: stage the stencil
+// cells (ghost cells by wrap / clamp) with their FP64/FP32 quantities, compute
+// the 64 Roe states once (one thread per face), then four 128-row tensor-core
+// batches of 16 faces x 4 fields x 2 sides.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "mlp_tc.cuh"
+#include "tc.cuh"
+
+namespace neno6 {
+namespace {
+
+using namespace tc;
+using namespace tcmlp;
+
+constexpr int kFaces = 64;       // faces per block
+constexpr int kMaxCells = 144;   // y block: 16 columns x (4 + 5) rows
+constexpr int kAlign = 128;
+
+constexpr int align_up(int x) { return (x + kAlign - 1) / kAlign * kAlign; }
+// dynamic shared-memory layout of the face kernel
+constexpr int kOffNet = 0;
+constexpr int kOffBufX = align_up(kOffNet + kNetImageBytes);
+constexpr int kOffBufY = align_up(kOffBufX + kBufXBytes);
+constexpr int kOffCellD = align_up(kOffBufY + kBufYBytes);      // 4 x kMaxCells doubles
+constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8); // 10 x kMaxCells floats
+constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16 floats
+constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 doubles
+constexpr int kOffGuard = align_up(kOffR + kFaces * 5 * 8);       // 4 warps x 128 floats
+constexpr int kOffBar = align_up(kOffGuard + 4 * 128 * 4);
+constexpr int kFacesSmem = kOffBar + 16;
+
+// per-cell arrays
+enum { CD_S = 0, CD_U = 1, CD_V = 2, CD_H = 3 };
+enum { CF_U = 0, CF_F = 4, CF_UN = 8, CF_C = 9 };
+
+__device__ __forceinline__ int wrap_idx(int i, int n, int bc) {
+  if (bc == 0) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// Warp-cooperative FP32 re-evaluation of the classifier for the rows of this
+// warp whose lane has `flagged` set (guard band).  gw: FP32 parameters with
+// every W transposed ([in][out]), biases after each W.  ws: 128 floats of
+// per-warp shared scratch.
+__device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* ws, const float (&x)[6],
+                                          float (&z)[4], bool flagged) {
+  const int lane = threadIdx.x & 31;
+  unsigned bal = __ballot_sync(0xffffffffu, flagged);
+  while (bal) {
+    const int src = __ffs(bal) - 1;
+    bal &= bal - 1;
+    float xs[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) xs[j] = __shfl_sync(0xffffffffu, x[j], src);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int o = lane + 32 * h;
+      float acc = gw[384 + o];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc = fmaf(gw[i * 64 + o], xs[i], acc);
+      ws[o] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+    {
+      float acc = gw[2496 + lane];
+#pragma unroll 8
+      for (int i = 0; i < 64; ++i) acc = fmaf(gw[448 + i * 32 + lane], ws[i], acc);
+      ws[64 + lane] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+    if (lane < 16) {
+      float acc = gw[3040 + lane];
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) acc = fmaf(gw[2528 + i * 16 + lane], ws[64 + i], acc);
+      ws[96 + lane] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+    if (lane < 8) {
+      float acc = gw[3184 + lane];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) acc = fmaf(gw[3056 + i * 8 + lane], ws[96 + i], acc);
+      ws[112 + lane] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+    if (lane < 4) {
+      float acc = gw[3224 + lane];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc = fmaf(gw[3192 + i * 4 + lane], ws[112 + i], acc);
+      ws[120 + lane] = acc;
+    }
+    __syncwarp();
+    if (lane == src) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z[k] = ws[120 + k];
+    }
+    __syncwarp();
+  }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
+  constexpr int NV = NDIM == 2 ? 4 : 3;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* s_net = smem + kOffNet;
+  double* cd = reinterpret_cast<double*>(smem + kOffCellD);
+  float* cf = reinterpret_cast<float*>(smem + kOffCellF);
+  float* sL = reinterpret_cast<float*>(smem + kOffL);
+  double* sR = reinterpret_cast<double*>(smem + kOffR);
+  float* ws = reinterpret_cast<float*>(smem + kOffGuard) + (threadIdx.x >> 5) * 128;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
+  const int t = threadIdx.x;
+  const int nx = a.nx, ny = a.ny;
+  const size_t plane = (size_t)nx * ny;
+  const double gm1 = a.gm1;
+  const float gamma_f = (float)a.gamma;
+
+  for (int i = t; i < kNetImageBytes / 16; i += kMlpThreads)
+    reinterpret_cast<uint4*>(s_net)[i] = reinterpret_cast<const uint4*>(a.net_image)[i];
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (t < 32) {
+    tmem_alloc(tmem_slot, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, a.bf16 != 0};
+  unsigned long long guarded = 0;
+  bool failed = false;
+
+  const long long nblk = a.nblk_x + a.nblk_y;
+  for (long long blk = blockIdx.x; blk < nblk && !failed; blk += gridDim.x) {
+    // ---- block geometry
+    const int dir = blk < a.nblk_x ? 0 : 1;
+    int row = 0, f0 = 0, i0 = 0, g0 = 0, ncells, cstride;
+    if (dir == 0) {
+      row = (int)(blk / a.bxf);
+      f0 = (int)(blk % a.bxf) * kFaces;
+      ncells = kFaces + 5;
+      cstride = 1;
+    } else {
+      const long long b = blk - a.nblk_x;
+      i0 = (int)(b % a.byc) * 16;
+      g0 = (int)(b / a.byc) * 4;
+      ncells = 16 * 9;
+      cstride = 16;
+    }
+    // ---- stencil cells: FP64 Roe inputs, FP32 reconstruction inputs
+    for (int c = t; c < ncells; c += kMlpThreads) {
+      int gi, gj;
+      if (dir == 0) {
+        gi = wrap_idx(f0 - 3 + c, nx, a.bcx);
+        gj = row;
+      } else {
+        gi = min(i0 + (c & 15), nx - 1);
+        gj = wrap_idx(g0 - 3 + (c >> 4), ny, a.bcy);
+      }
+      const size_t g = (size_t)gj * nx + gi;
+      double U[NV];
+#pragma unroll
+      for (int n = 0; n < NV; ++n) U[n] = a.U[n * plane + g];
+      const double rho = U[0], E = U[NV - 1];
+      const double rr = 1.0 / rho;
+      const double u = U[1] * rr;
+      const double v = NDIM == 2 ? U[2] * rr : 0.0;
+      const double q = NDIM == 2 ? fma(v, v, u * u) : u * u;
+      const double p = gm1 * (E - 0.5 * rho * q);
+      const double Ep = E + p;
+      if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.status, 1);
+      cd[CD_S * kMaxCells + c] = sqrt(rho);
+      cd[CD_U * kMaxCells + c] = u;
+      cd[CD_V * kMaxCells + c] = v;
+      cd[CD_H * kMaxCells + c] = Ep * rr;
+      double F[4];
+      if (NDIM == 1) {
+        F[0] = U[1]; F[1] = fma(U[1], u, p); F[2] = Ep * u; F[3] = 0.0;
+      } else if (dir == 0) {
+        F[0] = U[1]; F[1] = fma(U[1], u, p); F[2] = U[2] * u; F[3] = Ep * u;
+      } else {
+        F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        cf[(CF_U + n) * kMaxCells + c] = n < NV ? (float)U[n] : 0.0f;
+        cf[(CF_F + n) * kMaxCells + c] = (float)F[n];
+      }
+      cf[CF_UN * kMaxCells + c] = (float)(dir == 0 ? u : v);
+      cf[CF_C * kMaxCells + c] = sqrtf(gamma_f * (float)p / (float)rho);
+    }
+    __syncthreads();
+    // ---- Roe average and eigenvectors (FP64), one thread per face
+    if (t < kFaces) {
+      const int k = t;
+      const int cb0 = dir == 0 ? k : (k >> 4) * 16 + (k & 15);
+      const int ca = cb0 + 2 * cstride, cb = cb0 + 3 * cstride;
+      const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + (k >> 4) <= ny && i0 + (k & 15) < nx);
+      const double sa = cd[CD_S * kMaxCells + ca], sb = cd[CD_S * kMaxCells + cb];
+      const double rd = 1.0 / (sa + sb);
+      const double ut = fma(sb, cd[CD_U * kMaxCells + cb], sa * cd[CD_U * kMaxCells + ca]) * rd;
+      const double vt = fma(sb, cd[CD_V * kMaxCells + cb], sa * cd[CD_V * kMaxCells + ca]) * rd;
+      const double Ht = fma(sb, cd[CD_H * kMaxCells + cb], sa * cd[CD_H * kMaxCells + ca]) * rd;
+      const double qt = fma(vt, vt, ut * ut);
+      const double c2 = gm1 * (Ht - 0.5 * qt);
+      if (valid && !(c2 > 0.0)) atomicOr(a.status, 2);
+      const double ct = sqrt(c2);
+      const double ic = 1.0 / ct;
+      const double b1 = gm1 * ic * ic;
+      const double b2 = 0.5 * b1 * qt;
+      const double nt = dir == 0 ? ut : vt;
+      const double nc = nt * ic, b1u = b1 * ut, b1v = b1 * vt, hb1 = 0.5 * b1;
+      float* L = sL + k * 16;
+      if (NDIM == 1) {
+        L[0] = (float)(0.5 * (b2 + nc)); L[1] = (float)(0.5 * (-b1u - ic)); L[2] = (float)hb1; L[3] = 0.f;
+        L[4] = (float)(1.0 - b2); L[5] = (float)b1u; L[6] = (float)(-b1); L[7] = 0.f;
+        L[8] = (float)(0.5 * (b2 - nc)); L[9] = (float)(0.5 * (-b1u + ic)); L[10] = (float)hb1; L[11] = 0.f;
+        L[12] = L[13] = L[14] = L[15] = 0.f;
+      } else {
+        const double x0 = dir == 0 ? -ic : 0.0, y0 = dir == 0 ? 0.0 : -ic;
+        L[0] = (float)(0.5 * (b2 + nc)); L[1] = (float)(0.5 * (-b1u + x0)); L[2] = (float)(0.5 * (-b1v + y0));
+        L[3] = (float)hb1;
+        L[4] = (float)(1.0 - b2); L[5] = (float)b1u; L[6] = (float)b1v; L[7] = (float)(-b1);
+        L[8] = (float)(dir == 0 ? -vt : -ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
+        L[11] = 0.f;
+        L[12] = (float)(0.5 * (b2 - nc)); L[13] = (float)(0.5 * (-b1u - x0)); L[14] = (float)(0.5 * (-b1v - y0));
+        L[15] = (float)hb1;
+      }
+      double* R = sR + k * 5;
+      R[0] = ut; R[1] = vt; R[2] = Ht; R[3] = ct; R[4] = qt;
+    }
+    __syncthreads();
+    // ---- four tensor-core batches of 16 faces x 4 fields x 2 sides
+    for (int mt = 0; mt < kFaces / 16; ++mt) {
+      const int k = mt * 16 + (t >> 3);
+      const int fld = (t >> 1) & 3;
+      const int m = min(fld, NV - 1);
+      const int side = t & 1;
+      const int cb0 = dir == 0 ? k : (k >> 4) * 16 + (k & 15);
+      const bool valid = fld < NV && (dir == 0 ? (f0 + k <= nx) : (g0 + (k >> 4) <= ny && i0 + (k & 15) < nx));
+      const float* Lr = sL + k * 16 + m * 4;
+      float alpha = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int cj = cb0 + j * cstride;
+        const float un = cf[CF_UN * kMaxCells + cj], cs = cf[CF_C * kMaxCells + cj];
+        const float lam = m == 0 ? un - cs : (m == NV - 1 ? un + cs : un);
+        alpha = fmaxf(alpha, fabsf(lam));
+      }
+      const float sgn_alpha = side ? -alpha : alpha;
+      float s[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int cj = cb0 + j * cstride;
+        float vv = Lr[0] * cf[(CF_U + 0) * kMaxCells + cj];
+        float gg = Lr[0] * cf[(CF_F + 0) * kMaxCells + cj];
+#pragma unroll
+        for (int n = 1; n < NV; ++n) {
+          vv = fmaf(Lr[n], cf[(CF_U + n) * kMaxCells + cj], vv);
+          gg = fmaf(Lr[n], cf[(CF_F + n) * kMaxCells + cj], gg);
+        }
+        const float val = 0.5f * fmaf(sgn_alpha, vv, gg);
+        // "+" side: stencil i-2..i+3; "-" side: its mirror image
+        if (side == 0) s[j] = val;
+        else s[5 - j] = val;
+      }
+      float mx = 1.0f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) mx = fmaxf(mx, fabsf(s[j]));
+      const float inv = 1.0f / mx;
+      float x[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) x[j] = s[j] * inv;
+      unsigned eta;
+      if (a.mask_mode == kMaskMLP) {
+        st_row8(mc.bufY, t, 0, 16, pack2(x[0], x[1], mc.bf16), pack2(x[2], x[3], mc.bf16),
+                pack2(x[4], x[5], mc.bf16), 0u);
+        st_row8(mc.bufY, t, 8, 16, 0u, 0u, 0u, 0u);
+        fence_async_smem();
+        __syncthreads();
+        float z[4];
+        if (!mlp_tc(mc, z)) {
+          failed = true;
+          break;
+        }
+        if (a.guard_tau > 0.0f) {
+          bool flag = false;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) flag |= fabsf(z[q]) < a.guard_tau;
+          guarded += (flag && valid) ? 1 : 0;
+          guard_mlp(a.guard_w, ws, x, z, flag);
+        }
+        eta = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) eta |= (z[q] > 0.0f ? 1u : 0u) << q;
+      } else {
+        eta = a.mask_mode == kMaskRough ? 15u : 0u;
+      }
+      // candidates and renormalised combination (FP32); first-order fallback
+      float gsum;
+      if (eta == 15u) {
+        gsum = s[2];
+      } else {
+        float f[4];
+        f[0] = fmaf(a.cand[0][2], s[3], fmaf(a.cand[0][1], s[2], a.cand[0][0] * s[1]));
+        f[1] = fmaf(a.cand[1][2], s[4], fmaf(a.cand[1][1], s[3], a.cand[1][0] * s[2]));
+        f[2] = fmaf(a.cand[2][2], s[2], fmaf(a.cand[2][1], s[1], a.cand[2][0] * s[0]));
+        f[3] = fmaf(a.cand[3][3], s[5], fmaf(a.cand[3][2], s[4], fmaf(a.cand[3][1], s[3], a.cand[3][0] * s[2])));
+        gsum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (!((eta >> q) & 1u)) gsum = fmaf(a.wtab[eta][q], f[q], gsum);
+      }
+      const float gh = gsum + __shfl_xor_sync(0xffffffffu, gsum, 1);
+      const unsigned eta_other = __shfl_xor_sync(0xffffffffu, eta, 1);
+      double ghd[4];
+      const int fb = (t & 31) & ~7;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ghd[q] = (double)__shfl_sync(0xffffffffu, gh, fb + 2 * q);
+      if (side == 0 && valid) {
+        // back-projection F_n = sum_q R[n][q] gh_q (FP64), n = this lane's field
+        const double* Rd = sR + k * 5;
+        const double ut = Rd[0], vt = Rd[1], Ht = Rd[2], ct = Rd[3], qt = Rd[4];
+        const double nt = dir == 0 ? ut : vt;
+        const double ntc = nt * ct;
+        double R0, R1, R2, R3 = 0.0;
+        const int n = m;
+        if (NDIM == 1) {
+          if (n == 0) { R0 = 1.0; R1 = 1.0; R2 = 1.0; }
+          else if (n == 1) { R0 = ut - ct; R1 = ut; R2 = ut + ct; }
+          else { R0 = Ht - ntc; R1 = 0.5 * qt; R2 = Ht + ntc; }
+        } else if (n == 0) { R0 = 1.0; R1 = 1.0; R2 = 0.0; R3 = 1.0; }
+        else if (n == 3) { R0 = Ht - ntc; R1 = 0.5 * qt; R2 = dir == 0 ? vt : ut; R3 = Ht + ntc; }
+        else if ((n == 1) == (dir == 0)) {  // normal momentum component
+          R0 = nt - ct; R1 = nt; R2 = 0.0; R3 = nt + ct;
+        } else {                             // tangential momentum component
+          const double tt = dir == 0 ? vt : ut;
+          R0 = tt; R1 = tt; R2 = 1.0; R3 = tt;
+        }
+        double Fh = R0 * ghd[0];
+        Fh = fma(R1, ghd[1], Fh);
+        Fh = fma(R2, ghd[2], Fh);
+        if (NDIM == 2) Fh = fma(R3, ghd[3], Fh);
+        size_t idx;
+        if (dir == 0) {
+          const int f = f0 + k;
+          idx = ((size_t)n * ny + row) * (nx + 1) + f;
+          a.Fx[idx] = Fh;
+        } else {
+          const int g = g0 + (k >> 4), i = i0 + (k & 15);
+          idx = ((size_t)n * (ny + 1) + g) * nx + i;
+          a.Fy[idx] = Fh;
+          idx += (size_t)NV * ny * (nx + 1);
+        }
+        if (a.mask_out) a.mask_out[idx] = (uint8_t)(eta | (eta_other << 4));
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+  if (failed && t == 0) atomicOr(a.status, 4);
+  if (a.guard_count && guarded) atomicAdd(a.guard_count, guarded);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (t < 32) tmem_dealloc(*tmem_slot, 128);
+}
+
+// Conservative difference (FP64) and optional SSP-RK3 stage update.
+template <int NDIM>
+__global__ void __launch_bounds__(256) diff_mixed_kernel(DiffArgs a) {
+  constexpr int NV = NDIM == 2 ? 4 : 3;
+  const size_t plane = (size_t)a.nx * a.ny;
+  const size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double dt = a.stage ? *a.dt_dev : 0.0;
+  if (a.stage == 3 && cell == 0) *a.t_dev = *a.t_dev + dt;
+  if (cell >= plane) return;
+  const int i = (int)(cell % a.nx), j = (int)(cell / a.nx);
+#pragma unroll
+  for (int n = 0; n < NV; ++n) {
+    const size_t fx = ((size_t)n * a.ny + j) * (a.nx + 1) + i;
+    double r = -(a.Fx[fx + 1] - a.Fx[fx]) * a.inv_dx;
+    if (NDIM == 2) {
+      const size_t fy = ((size_t)n * (a.ny + 1) + j) * a.nx + i;
+      r -= (a.Fy[fy + a.nx] - a.Fy[fy]) * a.inv_dy;
+    }
+    const size_t e = n * plane + cell;
+    double val = r;
+    if (a.stage == 1) val = fma(dt, r, a.U[e]);
+    else if (a.stage == 2) val = fma(0.75, a.U0[e], 0.25 * fma(dt, r, a.U[e]));
+    else if (a.stage == 3) val = fma(a.third, a.U0[e], a.two_thirds * fma(dt, r, a.U[e]));
+    a.out[e] = val;
+  }
+}
+
+// dt = cfl / (max(|u|+c)/dx + max(|v|+c)/dy), clipped to t_end (one thread).
+__global__ void dt_kernel(const unsigned long long* smax, int ndim, double dx, double dy, double cfl,
+                          double t_end, const double* t_dev, double* dt_dev, double* dt_user) {
+  double s = __longlong_as_double((long long)smax[0]) / dx;
+  if (ndim == 2) s = s + __longlong_as_double((long long)smax[1]) / dy;
+  double dt = cfl / s;
+  const double t = *t_dev;
+  if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
+  *dt_dev = dt;
+  if (dt_user) *dt_user = dt;
+}
+
+}  // namespace
+
+void build_guard_image(const NetF64& net, float* g) {
+  const int widths[6] = {6, 64, 32, 16, 8, 4};
+  size_t p = 0;
+  for (int l = 0; l < 5; ++l) {
+    const int nin = widths[l], nout = widths[l + 1];
+    for (int o = 0; o < nout; ++o)
+      for (int i = 0; i < nin; ++i) g[p + (size_t)i * nout + o] = (float)net.p[p + (size_t)o * nin + i];
+    p += (size_t)nout * nin;
+    for (int o = 0; o < nout; ++o) g[p + o] = (float)net.p[p + o];
+    p += nout;
+  }
+}
+
+cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
+  a.bxf = (a.nx + 1 + kFaces - 1) / kFaces;
+  a.nblk_x = (long long)a.bxf * a.ny;
+  a.byc = (a.nx + 15) / 16;
+  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + 3) / 4) : 0;
+  const long long nblk = a.nblk_x + a.nblk_y;
+  const int blocks = (int)(nblk < 152 * 4 ? nblk : 152 * 4);
+  cudaError_t e;
+  if (ndim == 2) {
+    e = cudaFuncSetAttribute(faces_mixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);
+    if (e != cudaSuccess) return e;
+    faces_mixed_kernel<2><<<blocks, kMlpThreads, kFacesSmem, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(faces_mixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);
+    if (e != cudaSuccess) return e;
+    faces_mixed_kernel<1><<<blocks, kMlpThreads, kFacesSmem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s) {
+  const size_t cells = (size_t)a.nx * a.ny;
+  const unsigned blocks = (unsigned)((cells + 255) / 256);
+  if (ndim == 2) diff_mixed_kernel<2><<<blocks, 256, 0, s>>>(a);
+  else diff_mixed_kernel<1><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, double dy, double cfl, double t_end,
+                      const double* t_dev, double* dt_dev, double* dt_user, cudaStream_t s) {
+  dt_kernel<<<1, 1, 0, s>>>(smax, ndim, dx, dy, cfl, t_end, t_dev, dt_dev, dt_user);
+  return cudaGetLastError();
+}
+
+}  // namespace neno6
