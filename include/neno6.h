@@ -161,6 +161,26 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
                    double* logits, void* stream);
 
 /*
+ * neno6_rhs_vjp — adjoint of neno6_rhs with the classifier mask frozen:
+ * grad_U = J^T lambda, J = dL(U)/dU with the stencil-selection bits and the
+ * LLF alpha argmax (first index on ties) held at their values for U.  Not in
+ * the paper: the derivative of the scheme where the mask is locally
+ * constant.  Evaluated in FP64 for every precision; each face is recomputed
+ * from U (no stored intermediates) and differentiated exactly with
+ * forward-mode dual numbers; each cell gathers the contributions of the faces
+ * whose stencils contain it (no atomics, deterministic).
+ *   U       [nv][ny][nx] float64 state.
+ *   lambda  [nv][ny][nx] float64 cotangent of dU/dt.
+ *   mask    nullable; the frozen mask (layout of neno6_mask_bytes).  NULL:
+ *           recomputed from U by the FP64 classifier (bit-identical to
+ *           neno6_rhs of an FP64 handle).
+ *   grad_U  [nv][ny][nx] float64 out (must not alias U or lambda).
+ * Errors: ARG, ALIGN, CUDA.
+ */
+int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const uint8_t* mask,
+                  double* grad_U, void* stream);
+
+/*
  * neno6_status — synchronise `stream`, return the latched device status bits
  * (NENO6_STATUS_*) in *device_status and clear them.  Returns
  * NENO6_ERR_NONPHYSICAL when any bit was set, NENO6_ERR_CUDA when the stream

@@ -27,7 +27,8 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 0.5, "fp16": 0.1}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
-           "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc")
+           "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
+           "neno6_rhs_vjp")
 
 
 class Neno6Error(RuntimeError):
@@ -67,6 +68,7 @@ def load_library(path=LIB_PATH):
     lib.neno6_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     lib.neno6_last_error.argtypes = [vp]
     lib.neno6_last_error.restype = ctypes.c_char_p
+    lib.neno6_rhs_vjp.argtypes = [vp, dp, dp, u8p, dp, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
     _lib = lib
@@ -184,6 +186,19 @@ class Neno6:
                                              _stream()))
         return (eta, logits) if want_logits else eta
 
+    def rhs_vjp(self, U, lam, mask=None, out=None):
+        """J^T lam of the right-hand side at U with the classifier mask frozen
+        (recomputed from U by the FP64 classifier when mask is None)."""
+        U = self._state(U)
+        lam = self._state(lam.contiguous(), "lam")
+        out = torch.empty_like(U) if out is None else self._state(out, "out")
+        if mask is not None:
+            assert mask.dtype == torch.uint8 and mask.numel() == self.mask_bytes
+            mask = mask.contiguous()
+        self._check(self._lib.neno6_rhs_vjp(self._h, _ptr(U), _ptr(lam), _ptr(mask), _ptr(out),
+                                            _stream()))
+        return out
+
     def status(self):
         """Synchronise the current stream and return (and clear) the device
         status bits (1: non-physical cell, 2: non-physical Roe state)."""
@@ -192,3 +207,26 @@ class Neno6:
         if rc not in (OK, -6):
             self._check(rc)
         return v.value
+
+
+class RHS(torch.autograd.Function):
+    """dU/dt = L(U) as a differentiable function: the forward pass is
+    neno6_rhs (keeping its classifier mask), the backward pass the frozen-mask
+    adjoint neno6_rhs_vjp."""
+
+    @staticmethod
+    def forward(ctx, U, solver):
+        dUdt, mask = solver.rhs(U.contiguous(), want_mask=True)
+        ctx.solver = solver
+        ctx.save_for_backward(U, mask)
+        return dUdt
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        U, mask = ctx.saved_tensors
+        return ctx.solver.rhs_vjp(U.contiguous(), grad_out.contiguous(), mask=mask), None
+
+
+def rhs(U, solver):
+    """Differentiable NENO6 right-hand side (see RHS)."""
+    return RHS.apply(U, solver)

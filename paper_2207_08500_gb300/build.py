@@ -29,6 +29,7 @@ SOURCES = {
     "noalloc.cu": [],
     "mixed.cu": [],
     "mixed_rhs.cu": [],
+    "vjp.cu": ["-fmad=false"],
 }
 
 

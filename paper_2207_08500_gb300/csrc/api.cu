@@ -30,6 +30,8 @@ struct neno6_handle {
   uint8_t* d_net_image = nullptr;  // tensor-core classifier image (mixed precision)
   float* d_guard_w = nullptr;      // FP32 transposed parameters (guard band)
   double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
+  uint8_t* d_mask = nullptr;       // classifier mask of the adjoint's forward pass (lazily)
+  double* d_vjp_rhs = nullptr;     // dU/dt of that forward pass (lazily)
   unsigned long long* d_guard_count = nullptr;
   FacesMixedArgs faces_args;
   size_t state_elems = 0;
@@ -315,6 +317,8 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_guard_w);
   cudaFree(h->d_faces);
   cudaFree(h->d_guard_count);
+  cudaFree(h->d_mask);
+  cudaFree(h->d_vjp_rhs);
   delete h;
   return NENO6_OK;
 }
@@ -428,6 +432,40 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
   p.net = h->net;
   cudaError_t e = launch_classify_fp64(p, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "classify launch");
+  return NENO6_OK;
+}
+
+int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const uint8_t* mask,
+                  double* grad_U, void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (!U || !lambda || !grad_U) return fail(h, NENO6_ERR_ARG, "rhs_vjp: null pointer");
+  if (!aligned(U, 16) || !aligned(lambda, 16) || !aligned(grad_U, 16))
+    return fail(h, NENO6_ERR_ALIGN, "rhs_vjp: arrays must be 16-byte aligned");
+  if (grad_U == U || grad_U == lambda) return fail(h, NENO6_ERR_ARG, "rhs_vjp: grad_U must not alias an input");
+  cudaStream_t s = (cudaStream_t)stream;
+  RhsParamsF64& p = h->rhs_params;
+  if (!mask) {
+    // recompute the classifier mask of U with the FP64 path (bit-identical
+    // to the forward FP64 right-hand side)
+    cudaError_t e = cudaSuccess;
+    if (!h->d_mask) e = cudaMalloc(&h->d_mask, (size_t)neno6_mask_bytes(h));
+    if (e == cudaSuccess && !h->d_vjp_rhs) e = cudaMalloc(&h->d_vjp_rhs, h->state_elems * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp: mask buffers");
+    fill_rhs_args(h, p.a);
+    p.a.U = U;
+    p.a.out = h->d_vjp_rhs;
+    p.a.mask_out = h->d_mask;
+    p.a.stage = 0;
+    p.net = h->net;
+    e = launch_rhs_fp64(h->cfg.ndim, p, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp: forward");
+    mask = h->d_mask;
+  }
+  fill_rhs_args(h, p.a);
+  p.a.U = U;
+  p.a.mask_in = mask;
+  cudaError_t e = launch_rhs_vjp(h->cfg.ndim, p.a, lambda, grad_U, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp launch");
   return NENO6_OK;
 }
 

@@ -114,6 +114,7 @@ cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
                                   const uint8_t* net_image, bool bf16, int* status, cudaStream_t s);
 cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s);
+cudaError_t launch_rhs_vjp(int ndim, const RhsArgs& a, const double* lam, double* grad, cudaStream_t s);
 cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
                               unsigned long long* smax, int* status, cudaStream_t s);
 
