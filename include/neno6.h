@@ -181,6 +181,24 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
                   double* grad_U, void* stream);
 
 /*
+ * neno6_mlp_bwd — gradient of the classifier's training loss for retraining:
+ * the mean binary cross entropy of Eq. (Crossentropy) (mean over the n
+ * samples and the S = 4 outputs, sigmoid outputs of Sec. 3.1) with respect
+ * to every parameter of the handle's network, in FP32; the stencils are
+ * normalised as in Eq. (normalizainput) first.  Deterministic (fixed-order
+ * reductions).
+ *   X        [n][6] float64 stencil values.
+ *   labels   [n] uint8, bit k = eta_k (1: stencil S_k discarded).
+ *   n        1 <= n < 2^31.
+ *   grad     [3228] float32 out, weights-file order (per layer W[out][in]
+ *            then b[out]).
+ *   loss     nullable float32 scalar out: the loss itself.
+ * Errors: ARG, SHAPE, ALIGN, CUDA.
+ */
+int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, float* grad,
+                  float* loss, void* stream);
+
+/*
  * neno6_status — synchronise `stream`, return the latched device status bits
  * (NENO6_STATUS_*) in *device_status and clear them.  Returns
  * NENO6_ERR_NONPHYSICAL when any bit was set, NENO6_ERR_CUDA when the stream

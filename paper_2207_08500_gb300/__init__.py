@@ -28,7 +28,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 0.5, "fp16": 0.1}
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
-           "neno6_rhs_vjp")
+           "neno6_rhs_vjp", "neno6_mlp_bwd")
 
 
 class Neno6Error(RuntimeError):
@@ -69,6 +69,7 @@ def load_library(path=LIB_PATH):
     lib.neno6_last_error.argtypes = [vp]
     lib.neno6_last_error.restype = ctypes.c_char_p
     lib.neno6_rhs_vjp.argtypes = [vp, dp, dp, u8p, dp, vp]
+    lib.neno6_mlp_bwd.argtypes = [vp, dp, u8p, i64, vp, vp, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
     _lib = lib
@@ -198,6 +199,18 @@ class Neno6:
         self._check(self._lib.neno6_rhs_vjp(self._h, _ptr(U), _ptr(lam), _ptr(mask), _ptr(out),
                                             _stream()))
         return out
+
+    def mlp_bwd(self, X, labels):
+        """(grad [3228] float32, loss float32 tensor) of the mean BCE of the
+        classifier on raw stencils X [n, 6] float64 and label bits [n] uint8."""
+        assert X.is_cuda and X.dtype == torch.float64 and X.shape[-1] == 6
+        assert labels.is_cuda and labels.dtype == torch.uint8 and labels.numel() == X.shape[0]
+        X, labels = X.contiguous(), labels.contiguous()
+        grad = torch.empty(3228, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        self._check(self._lib.neno6_mlp_bwd(self._h, _ptr(X), _ptr(labels), X.shape[0], _ptr(grad),
+                                            _ptr(loss), _stream()))
+        return grad, loss
 
     def status(self):
         """Synchronise the current stream and return (and clear) the device

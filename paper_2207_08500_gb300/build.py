@@ -30,6 +30,7 @@ SOURCES = {
     "mixed.cu": [],
     "mixed_rhs.cu": [],
     "vjp.cu": ["-fmad=false"],
+    "mlp_bwd.cu": [],
 }
 
 

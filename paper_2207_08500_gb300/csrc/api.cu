@@ -32,6 +32,8 @@ struct neno6_handle {
   double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
   uint8_t* d_mask = nullptr;       // classifier mask of the adjoint's forward pass (lazily)
   double* d_vjp_rhs = nullptr;     // dU/dt of that forward pass (lazily)
+  float* d_params32 = nullptr;     // FP32 parameters, weights-file order
+  void* d_bwd_scratch = nullptr;   // per-CTA partial gradients (lazily)
   unsigned long long* d_guard_count = nullptr;
   FacesMixedArgs faces_args;
   size_t state_elems = 0;
@@ -282,6 +284,12 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
   if (e == cudaSuccess) e = cudaMalloc(&h->d_t, sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->d_t, 0, sizeof(double));
+  if (e == cudaSuccess) {
+    std::vector<float> p32(kNetParams);
+    for (int i = 0; i < kNetParams; ++i) p32[i] = (float)h->net.p[i];
+    e = cudaMalloc(&h->d_params32, kNetParams * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_params32, p32.data(), kNetParams * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess && c.precision != NENO6_FP64) {
     std::vector<uint8_t> img(kNetImageBytes);
     build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
@@ -319,6 +327,8 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_guard_count);
   cudaFree(h->d_mask);
   cudaFree(h->d_vjp_rhs);
+  cudaFree(h->d_params32);
+  cudaFree(h->d_bwd_scratch);
   delete h;
   return NENO6_OK;
 }
@@ -466,6 +476,25 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
   p.a.mask_in = mask;
   cudaError_t e = launch_rhs_vjp(h->cfg.ndim, p.a, lambda, grad_U, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp launch");
+  return NENO6_OK;
+}
+
+int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, float* grad, float* loss,
+                  void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (n < 1 || n >= (1ll << 31)) return fail(h, NENO6_ERR_SHAPE, "mlp_bwd: need 1 <= n < 2^31");
+  if (!X || !labels || !grad) return fail(h, NENO6_ERR_ARG, "mlp_bwd: null pointer");
+  if (!aligned(X, 8) || !aligned(grad, 4) || (loss && !aligned(loss, 4)))
+    return fail(h, NENO6_ERR_ALIGN, "mlp_bwd: misaligned");
+  if (!h->d_bwd_scratch) {
+    cudaError_t e = cudaMalloc(&h->d_bwd_scratch, mlp_bwd_scratch_bytes(1ll << 30));
+    if (e != cudaSuccess) {
+      h->d_bwd_scratch = nullptr;
+      return cuda_fail(h, e, "mlp_bwd: scratch");
+    }
+  }
+  cudaError_t e = launch_mlp_bwd(X, labels, n, h->d_params32, grad, loss, h->d_bwd_scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mlp_bwd launch");
   return NENO6_OK;
 }
 
