@@ -7,8 +7,9 @@ combination, back-projection, conservative difference, stage update).
 
 Default workload (N=1): 2D Euler, 4096 x 4096 periodic grid, seeded
 four-quadrant states with a sinusoidal density perturbation, mixed-precision
-path (bf16 tensor-core classifier, FP32 reconstruction, FP64 Roe
-eigenvectors / back-projection / difference / RK3).  Beside it the FP64 GPU
+path (fp16 tensor-core classifier with an FP32 guard band, FP32
+reconstruction of block-relative deviations, FP64 Roe eigenvectors, reference
+fluxes, difference and RK3).  Beside it the FP64 GPU
 path on the same state (speed, mask flip rate, L1/Linf error of dU/dt and of
 the state after one step).  `--precision fp64 --n 2048` gives the FP64 line.
 Metric: Mcell-updates/s (cells x steps / s), higher is better.
@@ -246,6 +247,38 @@ def run_ours(args, rank, world):
         ref.close()
         del A, B, S0, m64, mmx
 
+    # secondary rows (outside the timed region): the frozen-mask adjoint at
+    # 1024^2 and the classifier backward on 2^20 stencils
+    extra = {}
+    if not args.no_extra:
+        nv_ = 1024
+        g64 = neno6.Neno6(ndim=2, nx=nv_, ny=nv_, precision="fp64", weights=weights)
+        Uv = torch.from_numpy(synth.smooth_2d(nv_, nv_, seed=11)).to(dev)
+        lam = torch.from_numpy(synth.normal((4, nv_, nv_), seed=12)).to(dev)
+        _, maskv = g64.rhs(Uv, want_mask=True)
+        gv = g64.rhs_vjp(Uv, lam, mask=maskv)
+        e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        for _ in range(2):
+            g64.rhs_vjp(Uv, lam, mask=maskv, out=gv)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        vjp_ms = e_a.elapsed_time(e_b) / 2
+        extra["vjp_fp64_1024"] = {"ms_per_vjp": round(vjp_ms, 3),
+                                  "Mcell_evals_per_s": round(nv_ * nv_ / vjp_ms / 1e3, 3)}
+        Xs = torch.from_numpy(synth.mlp_stencils(1 << 20)).to(dev)
+        ys = torch.zeros(1 << 20, dtype=torch.uint8, device=dev)
+        ys[1 << 19:] = 0b1011
+        g64.mlp_bwd(Xs, ys)
+        e_a.record(stream)
+        for _ in range(3):
+            g64.mlp_bwd(Xs, ys)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        extra["mlp_bwd_2^20"] = {"ms_per_call": round(e_a.elapsed_time(e_b) / 3, 3)}
+        g64.close()
+        del Uv, lam, gv, maskv, Xs, ys
+
     # max over ranks
     vals = torch.tensor([ms, e2e_ms, rhs_avg], dtype=torch.float64, device=dev)
     if world > 1:
@@ -289,6 +322,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": launches_per_step * args.steps,
         "vs_fp64_gpu": compare,
+        "secondary": extra,
         "clocks": clock_info,
         "device_status": status,
     }
@@ -372,8 +406,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--precision", choices=["fp64", "bf16", "fp16"], default="bf16")
+    ap.add_argument("--precision", choices=["fp64", "bf16", "fp16"], default="fp16")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--rhs-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=48)

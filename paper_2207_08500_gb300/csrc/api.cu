@@ -231,6 +231,8 @@ int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, i
   d.nx = h->cfg.nx;
   d.ny = h->cfg.ny;
   d.stage = stage;
+  d.bcx = h->cfg.bc[0];
+  d.bcy = h->cfg.bc[1];
   d.inv_dx = 1.0 / h->cfg.dx;
   d.inv_dy = 1.0 / h->cfg.dy;
   d.third = 1.0 / 3.0;

@@ -102,6 +102,7 @@ struct DiffArgs {
   const double* dt_dev;
   double* t_dev;
   int nx, ny, stage;
+  int bcx, bcy;
   double inv_dx, inv_dy, third, two_thirds;
 };
 

@@ -16,10 +16,20 @@
 //
 // Face kernel: persistent CTAs of one warpgroup (up to four per SM, each with
 // 128 TMEM columns).  A block is 64 faces — 64 consecutive x faces of one
-// row, or 16 columns x 4 consecutive y faces.  Per block: stage the stencil
-// cells (ghost cells by wrap / clamp) with their FP64/FP32 quantities, compute
-// the 64 Roe states once (one thread per face), then four 128-row tensor-core
-// batches of 16 faces x 4 fields x 2 sides.
+// row, or 4 columns x 16 consecutive y faces.  Per block: stage the stencil
+// cells (ghost cells by wrap / clamp), compute the 64 Roe states once (one
+// thread per face, FP64), then four 128-row tensor-core batches of 16 faces x
+// 4 fields x 2 sides.
+//
+// Reference shift.  The block's first stencil cell is a reference state
+// (U_ref, F_ref); every cell is staged as the FP64 difference (U - U_ref,
+// F - F_ref) rounded to FP32.  The reconstruction is linear and reproduces
+// constants, and the alpha terms of the two sides cancel, so
+//   F_face = F_ref + R (g+(delta) + g-(delta))
+// exactly: FP32 rounding then acts on the small deviations of the block
+// rather than on O(1) fluxes, and the back-projection of the correction can
+// run in FP32 while F_ref is added in FP64.  The classifier still sees the
+// absolute split fluxes (reference part added back in FP32).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -34,7 +44,10 @@ using namespace tc;
 using namespace tcmlp;
 
 constexpr int kFaces = 64;       // faces per block
-constexpr int kMaxCells = 144;   // y block: 16 columns x (4 + 5) rows
+constexpr int kYCols = 4;        // y block: 4 columns x 16 faces
+constexpr int kYFaces = kFaces / kYCols;
+constexpr int kMaxCells = kYCols * (kYFaces + 5);  // 84 (x block: 69)
+static_assert(kMaxCells <= 128 && kFaces + 5 <= 128, "one stencil cell per thread");
 constexpr int kAlign = 128;
 
 constexpr int align_up(int x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -45,8 +58,9 @@ constexpr int kOffBufY = align_up(kOffBufX + kBufXBytes);
 constexpr int kOffCellD = align_up(kOffBufY + kBufYBytes);      // 4 x kMaxCells doubles
 constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8); // 10 x kMaxCells floats
 constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16 floats
-constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 doubles
-constexpr int kOffGuard = align_up(kOffR + kFaces * 5 * 8);       // 4 warps x 128 floats
+constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 floats
+constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
+constexpr int kOffGuard = align_up(kOffRef + 8 * 8 + 8 * 4);      // 4 warps x 128 floats
 constexpr int kOffBar = align_up(kOffGuard + 4 * 128 * 4);
 constexpr int kFacesSmem = kOffBar + 16;
 
@@ -129,7 +143,6 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   double* cd = reinterpret_cast<double*>(smem + kOffCellD);
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
-  double* sR = reinterpret_cast<double*>(smem + kOffR);
   float* ws = reinterpret_cast<float*>(smem + kOffGuard) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
@@ -157,6 +170,9 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   bool failed = false;
 
   const long long nblk = a.nblk_x + a.nblk_y;
+  double* refd = reinterpret_cast<double*>(smem + kOffRef);      // U_ref[4], F_ref[4] (FP64)
+  float* reff = reinterpret_cast<float*>(smem + kOffRef + 64);   // same, FP32
+  float* sRf = reinterpret_cast<float*>(smem + kOffR);           // ut, vt, Ht, ct, qt per face
   for (long long blk = blockIdx.x; blk < nblk && !failed; blk += gridDim.x) {
     // ---- block geometry
     const int dir = blk < a.nblk_x ? 0 : 1;
@@ -168,23 +184,23 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       cstride = 1;
     } else {
       const long long b = blk - a.nblk_x;
-      i0 = (int)(b % a.byc) * 16;
-      g0 = (int)(b / a.byc) * 4;
-      ncells = 16 * 9;
-      cstride = 16;
+      i0 = (int)(b % a.byc) * kYCols;
+      g0 = (int)(b / a.byc) * kYFaces;
+      ncells = kYCols * (kYFaces + 5);
+      cstride = kYCols;
     }
-    // ---- stencil cells: FP64 Roe inputs, FP32 reconstruction inputs
-    for (int c = t; c < ncells; c += kMlpThreads) {
+    // ---- stencil cells (one per thread): FP64 Roe inputs and fluxes
+    double U[NV], F[4];
+    if (t < ncells) {
       int gi, gj;
       if (dir == 0) {
-        gi = wrap_idx(f0 - 3 + c, nx, a.bcx);
+        gi = wrap_idx(f0 - 3 + t, nx, a.bcx);
         gj = row;
       } else {
-        gi = min(i0 + (c & 15), nx - 1);
-        gj = wrap_idx(g0 - 3 + (c >> 4), ny, a.bcy);
+        gi = min(i0 + (t % kYCols), nx - 1);
+        gj = wrap_idx(g0 - 3 + t / kYCols, ny, a.bcy);
       }
       const size_t g = (size_t)gj * nx + gi;
-      double U[NV];
 #pragma unroll
       for (int n = 0; n < NV; ++n) U[n] = a.U[n * plane + g];
       const double rho = U[0], E = U[NV - 1];
@@ -195,11 +211,10 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       const double p = gm1 * (E - 0.5 * rho * q);
       const double Ep = E + p;
       if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.status, 1);
-      cd[CD_S * kMaxCells + c] = sqrt(rho);
-      cd[CD_U * kMaxCells + c] = u;
-      cd[CD_V * kMaxCells + c] = v;
-      cd[CD_H * kMaxCells + c] = Ep * rr;
-      double F[4];
+      cd[CD_S * kMaxCells + t] = sqrt(rho);
+      cd[CD_U * kMaxCells + t] = u;
+      cd[CD_V * kMaxCells + t] = v;
+      cd[CD_H * kMaxCells + t] = Ep * rr;
       if (NDIM == 1) {
         F[0] = U[1]; F[1] = fma(U[1], u, p); F[2] = Ep * u; F[3] = 0.0;
       } else if (dir == 0) {
@@ -207,21 +222,33 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       } else {
         F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
       }
+      cf[CF_UN * kMaxCells + t] = (float)(dir == 0 ? u : v);
+      cf[CF_C * kMaxCells + t] = sqrtf(gamma_f * (float)p / (float)rho);
+      if (t == 0) {  // the block's reference state
 #pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        cf[(CF_U + n) * kMaxCells + c] = n < NV ? (float)U[n] : 0.0f;
-        cf[(CF_F + n) * kMaxCells + c] = (float)F[n];
+        for (int n = 0; n < 4; ++n) {
+          refd[n] = n < NV ? U[n] : 0.0;
+          refd[4 + n] = F[n];
+          reff[n] = n < NV ? (float)U[n] : 0.0f;
+          reff[4 + n] = (float)F[n];
+        }
       }
-      cf[CF_UN * kMaxCells + c] = (float)(dir == 0 ? u : v);
-      cf[CF_C * kMaxCells + c] = sqrtf(gamma_f * (float)p / (float)rho);
     }
     __syncthreads();
+    // ---- deviations from the reference, rounded to FP32
+    if (t < ncells) {
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        cf[(CF_U + n) * kMaxCells + t] = n < NV ? (float)(U[n] - refd[n]) : 0.0f;
+        cf[(CF_F + n) * kMaxCells + t] = (float)(F[n] - refd[4 + n]);
+      }
+    }
     // ---- Roe average and eigenvectors (FP64), one thread per face
     if (t < kFaces) {
       const int k = t;
-      const int cb0 = dir == 0 ? k : (k >> 4) * 16 + (k & 15);
+      const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
       const int ca = cb0 + 2 * cstride, cb = cb0 + 3 * cstride;
-      const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + (k >> 4) <= ny && i0 + (k & 15) < nx);
+      const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx);
       const double sa = cd[CD_S * kMaxCells + ca], sb = cd[CD_S * kMaxCells + cb];
       const double rd = 1.0 / (sa + sb);
       const double ut = fma(sb, cd[CD_U * kMaxCells + cb], sa * cd[CD_U * kMaxCells + ca]) * rd;
@@ -252,8 +279,8 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
         L[12] = (float)(0.5 * (b2 - nc)); L[13] = (float)(0.5 * (-b1u - x0)); L[14] = (float)(0.5 * (-b1v - y0));
         L[15] = (float)hb1;
       }
-      double* R = sR + k * 5;
-      R[0] = ut; R[1] = vt; R[2] = Ht; R[3] = ct; R[4] = qt;
+      float* R = sRf + k * 5;
+      R[0] = (float)ut; R[1] = (float)vt; R[2] = (float)Ht; R[3] = (float)ct; R[4] = (float)qt;
     }
     __syncthreads();
     // ---- four tensor-core batches of 16 faces x 4 fields x 2 sides
@@ -262,8 +289,9 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       const int fld = (t >> 1) & 3;
       const int m = min(fld, NV - 1);
       const int side = t & 1;
-      const int cb0 = dir == 0 ? k : (k >> 4) * 16 + (k & 15);
-      const bool valid = fld < NV && (dir == 0 ? (f0 + k <= nx) : (g0 + (k >> 4) <= ny && i0 + (k & 15) < nx));
+      const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
+      const bool valid = fld < NV &&
+                         (dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx));
       const float* Lr = sL + k * 16 + m * 4;
       float alpha = 0.0f;
 #pragma unroll
@@ -274,7 +302,15 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
         alpha = fmaxf(alpha, fabsf(lam));
       }
       const float sgn_alpha = side ? -alpha : alpha;
-      float s[6];
+      // reference part of this side's split flux: (L F_ref +- alpha L U_ref)/2
+      float vr = Lr[0] * reff[0], gr = Lr[0] * reff[4];
+#pragma unroll
+      for (int n = 1; n < NV; ++n) {
+        vr = fmaf(Lr[n], reff[n], vr);
+        gr = fmaf(Lr[n], reff[4 + n], gr);
+      }
+      const float cref = 0.5f * fmaf(sgn_alpha, vr, gr);
+      float ds[6];  // deviations of the split flux from the reference part
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
         const int cj = cb0 + j * cstride;
@@ -287,12 +323,15 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
         }
         const float val = 0.5f * fmaf(sgn_alpha, vv, gg);
         // "+" side: stencil i-2..i+3; "-" side: its mirror image
-        if (side == 0) s[j] = val;
-        else s[5 - j] = val;
+        if (side == 0) ds[j] = val;
+        else ds[5 - j] = val;
       }
-      float mx = 1.0f;
+      float mx = 1.0f, s[6];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) mx = fmaxf(mx, fabsf(s[j]));
+      for (int j = 0; j < 6; ++j) {
+        s[j] = cref + ds[j];
+        mx = fmaxf(mx, fabsf(s[j]));
+      }
       const float inv = 1.0f / mx;
       float x[6];
 #pragma unroll
@@ -322,16 +361,17 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       } else {
         eta = a.mask_mode == kMaskRough ? 15u : 0u;
       }
-      // candidates and renormalised combination (FP32); first-order fallback
+      // candidates and renormalised combination of the deviations (FP32);
+      // first-order fallback
       float gsum;
       if (eta == 15u) {
-        gsum = s[2];
+        gsum = ds[2];
       } else {
         float f[4];
-        f[0] = fmaf(a.cand[0][2], s[3], fmaf(a.cand[0][1], s[2], a.cand[0][0] * s[1]));
-        f[1] = fmaf(a.cand[1][2], s[4], fmaf(a.cand[1][1], s[3], a.cand[1][0] * s[2]));
-        f[2] = fmaf(a.cand[2][2], s[2], fmaf(a.cand[2][1], s[1], a.cand[2][0] * s[0]));
-        f[3] = fmaf(a.cand[3][3], s[5], fmaf(a.cand[3][2], s[4], fmaf(a.cand[3][1], s[3], a.cand[3][0] * s[2])));
+        f[0] = fmaf(a.cand[0][2], ds[3], fmaf(a.cand[0][1], ds[2], a.cand[0][0] * ds[1]));
+        f[1] = fmaf(a.cand[1][2], ds[4], fmaf(a.cand[1][1], ds[3], a.cand[1][0] * ds[2]));
+        f[2] = fmaf(a.cand[2][2], ds[2], fmaf(a.cand[2][1], ds[1], a.cand[2][0] * ds[0]));
+        f[3] = fmaf(a.cand[3][3], ds[5], fmaf(a.cand[3][2], ds[4], fmaf(a.cand[3][1], ds[3], a.cand[3][0] * ds[2])));
         gsum = 0.0f;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -339,41 +379,42 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       }
       const float gh = gsum + __shfl_xor_sync(0xffffffffu, gsum, 1);
       const unsigned eta_other = __shfl_xor_sync(0xffffffffu, eta, 1);
-      double ghd[4];
+      float ghq[4];
       const int fb = (t & 31) & ~7;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) ghd[q] = (double)__shfl_sync(0xffffffffu, gh, fb + 2 * q);
+      for (int q = 0; q < 4; ++q) ghq[q] = __shfl_sync(0xffffffffu, gh, fb + 2 * q);
       if (side == 0 && valid) {
-        // back-projection F_n = sum_q R[n][q] gh_q (FP64), n = this lane's field
-        const double* Rd = sR + k * 5;
-        const double ut = Rd[0], vt = Rd[1], Ht = Rd[2], ct = Rd[3], qt = Rd[4];
-        const double nt = dir == 0 ? ut : vt;
-        const double ntc = nt * ct;
-        double R0, R1, R2, R3 = 0.0;
+        // back-projection of the correction (FP32), plus F_ref (FP64)
+        const float* Rd = sRf + k * 5;
+        const float ut = Rd[0], vt = Rd[1], Ht = Rd[2], ct = Rd[3], qt = Rd[4];
+        const float nt = dir == 0 ? ut : vt;
+        const float ntc = nt * ct;
+        float R0, R1, R2, R3 = 0.0f;
         const int n = m;
         if (NDIM == 1) {
-          if (n == 0) { R0 = 1.0; R1 = 1.0; R2 = 1.0; }
+          if (n == 0) { R0 = 1.0f; R1 = 1.0f; R2 = 1.0f; }
           else if (n == 1) { R0 = ut - ct; R1 = ut; R2 = ut + ct; }
-          else { R0 = Ht - ntc; R1 = 0.5 * qt; R2 = Ht + ntc; }
-        } else if (n == 0) { R0 = 1.0; R1 = 1.0; R2 = 0.0; R3 = 1.0; }
-        else if (n == 3) { R0 = Ht - ntc; R1 = 0.5 * qt; R2 = dir == 0 ? vt : ut; R3 = Ht + ntc; }
+          else { R0 = Ht - ntc; R1 = 0.5f * qt; R2 = Ht + ntc; }
+        } else if (n == 0) { R0 = 1.0f; R1 = 1.0f; R2 = 0.0f; R3 = 1.0f; }
+        else if (n == 3) { R0 = Ht - ntc; R1 = 0.5f * qt; R2 = dir == 0 ? vt : ut; R3 = Ht + ntc; }
         else if ((n == 1) == (dir == 0)) {  // normal momentum component
-          R0 = nt - ct; R1 = nt; R2 = 0.0; R3 = nt + ct;
+          R0 = nt - ct; R1 = nt; R2 = 0.0f; R3 = nt + ct;
         } else {                             // tangential momentum component
-          const double tt = dir == 0 ? vt : ut;
-          R0 = tt; R1 = tt; R2 = 1.0; R3 = tt;
+          const float tt = dir == 0 ? vt : ut;
+          R0 = tt; R1 = tt; R2 = 1.0f; R3 = tt;
         }
-        double Fh = R0 * ghd[0];
-        Fh = fma(R1, ghd[1], Fh);
-        Fh = fma(R2, ghd[2], Fh);
-        if (NDIM == 2) Fh = fma(R3, ghd[3], Fh);
+        float corr = R0 * ghq[0];
+        corr = fmaf(R1, ghq[1], corr);
+        corr = fmaf(R2, ghq[2], corr);
+        if (NDIM == 2) corr = fmaf(R3, ghq[3], corr);
+        const double Fh = refd[4 + n] + (double)corr;
         size_t idx;
         if (dir == 0) {
           const int f = f0 + k;
           idx = ((size_t)n * ny + row) * (nx + 1) + f;
           a.Fx[idx] = Fh;
         } else {
-          const int g = g0 + (k >> 4), i = i0 + (k & 15);
+          const int g = g0 + k / kYCols, i = i0 + k % kYCols;
           idx = ((size_t)n * (ny + 1) + g) * nx + i;
           a.Fy[idx] = Fh;
           idx += (size_t)NV * ny * (nx + 1);
@@ -404,11 +445,15 @@ __global__ void __launch_bounds__(256) diff_mixed_kernel(DiffArgs a) {
   const int i = (int)(cell % a.nx), j = (int)(cell / a.nx);
 #pragma unroll
   for (int n = 0; n < NV; ++n) {
+    // with periodic boundaries faces 0 and nx (ny) are one physical face:
+    // both neighbours use face 0's value, so the difference telescopes exactly
     const size_t fx = ((size_t)n * a.ny + j) * (a.nx + 1) + i;
-    double r = -(a.Fx[fx + 1] - a.Fx[fx]) * a.inv_dx;
+    const size_t fxr = (i + 1 == a.nx && a.bcx == 0) ? fx + 1 - a.nx : fx + 1;
+    double r = -(a.Fx[fxr] - a.Fx[fx]) * a.inv_dx;
     if (NDIM == 2) {
       const size_t fy = ((size_t)n * (a.ny + 1) + j) * a.nx + i;
-      r -= (a.Fy[fy + a.nx] - a.Fy[fy]) * a.inv_dy;
+      const size_t fyr = (j + 1 == a.ny && a.bcy == 0) ? fy + a.nx - (size_t)a.ny * a.nx : fy + a.nx;
+      r -= (a.Fy[fyr] - a.Fy[fy]) * a.inv_dy;
     }
     const size_t e = n * plane + cell;
     double val = r;
@@ -449,8 +494,8 @@ void build_guard_image(const NetF64& net, float* g) {
 cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
   a.bxf = (a.nx + 1 + kFaces - 1) / kFaces;
   a.nblk_x = (long long)a.bxf * a.ny;
-  a.byc = (a.nx + 15) / 16;
-  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + 3) / 4) : 0;
+  a.byc = (a.nx + kYCols - 1) / kYCols;
+  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kYFaces - 1) / kYFaces) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
   const int blocks = (int)(nblk < 152 * 4 ? nblk : 152 * 4);
   cudaError_t e;

@@ -79,8 +79,10 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bi
     uint32_t p[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float a = fmaxf(__uint_as_float(r[2 * i]) + bias[16 * c16 + 2 * i], 0.0f);
-      const float b = fmaxf(__uint_as_float(r[2 * i + 1]) + bias[16 * c16 + 2 * i + 1], 0.0f);
+      // ReLU; fp16 activations are also kept below the fp16 maximum
+      const float hi = c.bf16 ? 3.0e38f : 65000.0f;
+      const float a = fminf(fmaxf(__uint_as_float(r[2 * i]) + bias[16 * c16 + 2 * i], 0.0f), hi);
+      const float b = fminf(fmaxf(__uint_as_float(r[2 * i + 1]) + bias[16 * c16 + 2 * i + 1], 0.0f), hi);
       p[i] = pack2(a, b, c.bf16);
     }
     st_row8(Anext, t, 16 * c16, N, p[0], p[1], p[2], p[3]);
