@@ -383,19 +383,27 @@ def run_reference(args):
 
 
 def run_rhs_only(args):
-    """`--rhs-only`: warm-up + `--steps` plain RHS evaluations (a case for
-    profilers); prints one line, no timing."""
+    """`--rhs-only` / `--vjp-only`: warm-up + `--steps` plain RHS (or
+    frozen-mask adjoint) evaluations, a case for profilers; prints one line,
+    no timing."""
     import torch
     import paper_2207_08500_gb300 as neno6
     import synth
     n = args.n
-    g = neno6.Neno6(ndim=2, nx=n, ny=n, precision=args.precision, weights=args.weights)
+    prec = "fp64" if args.vjp_only else args.precision
+    g = neno6.Neno6(ndim=2, nx=n, ny=n, precision=prec, weights=args.weights)
     U = torch.from_numpy(synth.quadrants_2d(n, n)).cuda()
     d = torch.empty_like(U)
+    if args.vjp_only:
+        lam = torch.from_numpy(synth.normal(U.shape, seed=12)).cuda()
+        _, mask = g.rhs(U, want_mask=True)
     for _ in range(args.warmup + args.steps):
-        g.rhs(U, out=d)
+        if args.vjp_only:
+            g.rhs_vjp(U, lam, mask=mask, out=d)
+        else:
+            g.rhs(U, out=d)
     torch.cuda.synchronize()
-    print(json.dumps({"rhs_only": True, "n": n, "precision": args.precision,
+    print(json.dumps({"vjp_only" if args.vjp_only else "rhs_only": True, "n": n, "precision": prec,
                       "launches": args.warmup + args.steps, "status": g.status()}))
 
 
@@ -410,6 +418,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--rhs-only", action="store_true")
+    ap.add_argument("--vjp-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--cpu-crop", type=int, default=96)
@@ -417,7 +426,7 @@ def main():
     if args.n is None:
         args.n = 2048 if args.precision == "fp64" else 4096
 
-    if args.rhs_only:
+    if args.rhs_only or args.vjp_only:
         run_rhs_only(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

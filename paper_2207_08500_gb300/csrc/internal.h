@@ -55,16 +55,18 @@ struct ClassifyParamsF64 {
   NetF64 net;
 };
 
-// Tensor-core image of the classifier (mixed precision): 16-bit B operands
-// W_l[out][in] in the K-major canonical layout (N and K padded to multiples
-// of 16), then the FP32 biases at columns 0 / 64 / 96 / 112 / 128.
-constexpr int kNetImageB1 = 0;                         // 64 x 16
+// Tensor-core image of the classifier (mixed precision): layers 1-3 as 16-bit
+// B operands W_l[out][in] in the K-major canonical layout (K of layer 1
+// padded 6 -> 16), then all FP32 biases (b1 at 0, b2 at 64, b3 at 96, b4 at
+// 112, b5 at 120), then the FP32 weights of layers 4 and 5 (W4[8][16],
+// W5[4][8]), which run on the CUDA cores.
+constexpr int kNetImageB1 = 0;                          // 64 x 16
 constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;  // 32 x 64
 constexpr int kNetImageB3 = kNetImageB2 + 32 * 64 * 2;  // 16 x 32
-constexpr int kNetImageB4 = kNetImageB3 + 16 * 32 * 2;  // 16 x 16 (8 real rows)
-constexpr int kNetImageB5 = kNetImageB4 + 16 * 16 * 2;  // 16 x 16 (4 x 8 real)
-constexpr int kNetImageBias = kNetImageB5 + 16 * 16 * 2;
-constexpr int kNetImageBytes = kNetImageBias + 144 * 4;
+constexpr int kNetImageBias = kNetImageB3 + 16 * 32 * 2;
+constexpr int kNetImageW4 = kNetImageBias + 128 * 4;
+constexpr int kNetImageW5 = kNetImageW4 + 8 * 16 * 4;
+constexpr int kNetImageBytes = kNetImageW5 + 4 * 8 * 4;
 static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");
 
 void build_net_image(const NetF64& net, bool bf16, uint8_t* img);

@@ -41,11 +41,13 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
   __shared__ __align__(128) uint8_t s_bufY[kBufYBytes];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tmem;
+  __shared__ int s_fail;
   const int t = threadIdx.x;
   load_net_image(s_net, net_image);
   if (t == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
+    s_fail = 0;
   }
   if (t < 32) {
     tmem_alloc(&s_tmem, 128);
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx c{s_net, s_bufX, s_bufY, &s_bar, s_tmem, 0u, bf16 != 0};
+  MlpCtx c{s_net, s_bufX, s_bufY, &s_bar, s_tmem, 0u, bf16 != 0, &s_fail};
   const long long tiles = (n + 127) / 128;
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long r = tile * 128 + t;
@@ -119,21 +121,27 @@ uint16_t to_fp16_bits(double d) {
 // Host: lay the FP64 master parameters out as the tensor-core image.
 void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
   std::memset(img, 0, kNetImageBytes);
-  auto put = [&](int off, int N, int K, int n, int k, double w) {
+  auto put = [&](int off, int K, int n, int k, double w) {
     const uint16_t b = bf16 ? to_bf16_bits(w) : to_fp16_bits(w);
     std::memcpy(img + off + kmajor_offset(n, k, K), &b, 2);
   };
   const int widths[6] = {6, 64, 32, 16, 8, 4};
-  const int boff[5] = {kNetImageB1, kNetImageB2, kNetImageB3, kNetImageB4, kNetImageB5};
-  const int Kpad[5] = {16, 64, 32, 16, 16};
-  const int Npad[5] = {64, 32, 16, 16, 16};
-  const int bias_off[5] = {0, 64, 96, 112, 128};
+  const int boff[3] = {kNetImageB1, kNetImageB2, kNetImageB3};
+  const int Kpad[3] = {16, 64, 32};
+  const int bias_off[5] = {0, 64, 96, 112, 120};
   float* bias = reinterpret_cast<float*>(img + kNetImageBias);
+  float* w4 = reinterpret_cast<float*>(img + kNetImageW4);
+  float* w5 = reinterpret_cast<float*>(img + kNetImageW5);
   size_t p = 0;
   for (int l = 0; l < 5; ++l) {
     const int nin = widths[l], nout = widths[l + 1];
     for (int o = 0; o < nout; ++o)
-      for (int i = 0; i < nin; ++i) put(boff[l], Npad[l], Kpad[l], o, i, net.p[p + (size_t)o * nin + i]);
+      for (int i = 0; i < nin; ++i) {
+        const double w = net.p[p + (size_t)o * nin + i];
+        if (l < 3) put(boff[l], Kpad[l], o, i, w);
+        else if (l == 3) w4[o * 16 + i] = (float)w;
+        else w5[o * 8 + i] = (float)w;
+      }
     p += (size_t)nout * nin;
     for (int o = 0; o < nout; ++o) bias[bias_off[l] + o] = (float)net.p[p + o];
     p += nout;

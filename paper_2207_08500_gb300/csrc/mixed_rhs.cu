@@ -76,6 +76,50 @@ __device__ __forceinline__ int wrap_idx(int i, int n, int bc) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// FP64 helpers of the mixed path (results within ~1 ulp; the mixed path
+// does not need correctly rounded divisions): hardware reciprocal / reciprocal
+// square-root approximations refined by two Newton steps.
+__device__ __forceinline__ double rcp64(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ double rsqrt64(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-x, y * y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+// binary64 -> binary32, round to nearest even, on the integer pipe (values
+// below the FP32 normal range flush to zero; no overflow in this use).
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e < 897) return __uint_as_float(sign);
+  const unsigned long long m = b & 0x000fffffffffffffull;
+  const unsigned long long r = m + 0x0fffffffull + ((m >> 29) & 1ull);
+  return __uint_as_float(sign | (((unsigned)(e - 896) << 23) + (unsigned)(r >> 29)));
+}
+// binary32 -> binary64 (exact), on the integer pipe; zero and normal values.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 // Warp-cooperative FP32 re-evaluation of the classifier for the rows of this
 // warp whose lane has `flagged` set (guard band).  gw: FP32 parameters with
 // every W transposed ([in][out]), biases after each W.  ws: 128 floats of
@@ -146,6 +190,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   float* ws = reinterpret_cast<float*>(smem + kOffGuard) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
+  int* fail_flag = reinterpret_cast<int*>(smem + kOffBar + 12);
   const int t = threadIdx.x;
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
@@ -157,6 +202,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   if (t == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    *fail_flag = 0;
   }
   if (t < 32) {
     tmem_alloc(tmem_slot, 128);
@@ -165,7 +211,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, a.bf16 != 0};
+  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, a.bf16 != 0, fail_flag};
   unsigned long long guarded = 0;
   bool failed = false;
 
@@ -189,32 +235,37 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       ncells = kYCols * (kYFaces + 5);
       cstride = kYCols;
     }
+    // thread index rotated by one warp per block, so that the partly
+    // occupied cell and Roe phases fall on different warps (and SM
+    // sub-partitions) from block to block
+    const int tr = (t + (int)((blk & 3) * 32)) & (kMlpThreads - 1);
     // ---- stencil cells (one per thread): FP64 Roe inputs and fluxes
     double U[NV], F[4];
-    if (t < ncells) {
+    if (tr < ncells) {
       int gi, gj;
       if (dir == 0) {
-        gi = wrap_idx(f0 - 3 + t, nx, a.bcx);
+        gi = wrap_idx(f0 - 3 + tr, nx, a.bcx);
         gj = row;
       } else {
-        gi = min(i0 + (t % kYCols), nx - 1);
-        gj = wrap_idx(g0 - 3 + t / kYCols, ny, a.bcy);
+        gi = min(i0 + (tr % kYCols), nx - 1);
+        gj = wrap_idx(g0 - 3 + tr / kYCols, ny, a.bcy);
       }
       const size_t g = (size_t)gj * nx + gi;
 #pragma unroll
       for (int n = 0; n < NV; ++n) U[n] = a.U[n * plane + g];
       const double rho = U[0], E = U[NV - 1];
-      const double rr = 1.0 / rho;
+      const double rs = rsqrt64(rho);  // 1/sqrt(rho)
+      const double rr = rs * rs;       // 1/rho
       const double u = U[1] * rr;
       const double v = NDIM == 2 ? U[2] * rr : 0.0;
       const double q = NDIM == 2 ? fma(v, v, u * u) : u * u;
       const double p = gm1 * (E - 0.5 * rho * q);
       const double Ep = E + p;
       if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.status, 1);
-      cd[CD_S * kMaxCells + t] = sqrt(rho);
-      cd[CD_U * kMaxCells + t] = u;
-      cd[CD_V * kMaxCells + t] = v;
-      cd[CD_H * kMaxCells + t] = Ep * rr;
+      cd[CD_S * kMaxCells + tr] = rho * rs;  // sqrt(rho)
+      cd[CD_U * kMaxCells + tr] = u;
+      cd[CD_V * kMaxCells + tr] = v;
+      cd[CD_H * kMaxCells + tr] = Ep * rr;
       if (NDIM == 1) {
         F[0] = U[1]; F[1] = fma(U[1], u, p); F[2] = Ep * u; F[3] = 0.0;
       } else if (dir == 0) {
@@ -222,65 +273,66 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
       } else {
         F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
       }
-      cf[CF_UN * kMaxCells + t] = (float)(dir == 0 ? u : v);
-      cf[CF_C * kMaxCells + t] = sqrtf(gamma_f * (float)p / (float)rho);
-      if (t == 0) {  // the block's reference state
+      cf[CF_UN * kMaxCells + tr] = d2f(dir == 0 ? u : v);
+      cf[CF_C * kMaxCells + tr] = sqrtf(gamma_f * d2f(p) * d2f(rr));
+      if (tr == 0) {  // the block's reference state
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
           refd[n] = n < NV ? U[n] : 0.0;
           refd[4 + n] = F[n];
-          reff[n] = n < NV ? (float)U[n] : 0.0f;
-          reff[4 + n] = (float)F[n];
+          reff[n] = n < NV ? d2f(U[n]) : 0.0f;
+          reff[4 + n] = d2f(F[n]);
         }
       }
     }
     __syncthreads();
     // ---- deviations from the reference, rounded to FP32
-    if (t < ncells) {
+    if (tr < ncells) {
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
-        cf[(CF_U + n) * kMaxCells + t] = n < NV ? (float)(U[n] - refd[n]) : 0.0f;
-        cf[(CF_F + n) * kMaxCells + t] = (float)(F[n] - refd[4 + n]);
+        cf[(CF_U + n) * kMaxCells + tr] = n < NV ? d2f(U[n] - refd[n]) : 0.0f;
+        cf[(CF_F + n) * kMaxCells + tr] = d2f(F[n] - refd[4 + n]);
       }
     }
     // ---- Roe average and eigenvectors (FP64), one thread per face
-    if (t < kFaces) {
-      const int k = t;
+    const int tq = (tr + 64) & (kMlpThreads - 1);  // the other half of the CTA
+    if (tq < kFaces) {
+      const int k = tq;
       const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
       const int ca = cb0 + 2 * cstride, cb = cb0 + 3 * cstride;
       const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx);
       const double sa = cd[CD_S * kMaxCells + ca], sb = cd[CD_S * kMaxCells + cb];
-      const double rd = 1.0 / (sa + sb);
+      const double rd = rcp64(sa + sb);
       const double ut = fma(sb, cd[CD_U * kMaxCells + cb], sa * cd[CD_U * kMaxCells + ca]) * rd;
       const double vt = fma(sb, cd[CD_V * kMaxCells + cb], sa * cd[CD_V * kMaxCells + ca]) * rd;
       const double Ht = fma(sb, cd[CD_H * kMaxCells + cb], sa * cd[CD_H * kMaxCells + ca]) * rd;
       const double qt = fma(vt, vt, ut * ut);
       const double c2 = gm1 * (Ht - 0.5 * qt);
       if (valid && !(c2 > 0.0)) atomicOr(a.status, 2);
-      const double ct = sqrt(c2);
-      const double ic = 1.0 / ct;
+      const double ic = rsqrt64(c2);  // 1/c
+      const double ct = c2 * ic;
       const double b1 = gm1 * ic * ic;
       const double b2 = 0.5 * b1 * qt;
       const double nt = dir == 0 ? ut : vt;
       const double nc = nt * ic, b1u = b1 * ut, b1v = b1 * vt, hb1 = 0.5 * b1;
       float* L = sL + k * 16;
       if (NDIM == 1) {
-        L[0] = (float)(0.5 * (b2 + nc)); L[1] = (float)(0.5 * (-b1u - ic)); L[2] = (float)hb1; L[3] = 0.f;
-        L[4] = (float)(1.0 - b2); L[5] = (float)b1u; L[6] = (float)(-b1); L[7] = 0.f;
-        L[8] = (float)(0.5 * (b2 - nc)); L[9] = (float)(0.5 * (-b1u + ic)); L[10] = (float)hb1; L[11] = 0.f;
+        L[0] = d2f(0.5 * (b2 + nc)); L[1] = d2f(0.5 * (-b1u - ic)); L[2] = d2f(hb1); L[3] = 0.f;
+        L[4] = d2f(1.0 - b2); L[5] = d2f(b1u); L[6] = d2f(-b1); L[7] = 0.f;
+        L[8] = d2f(0.5 * (b2 - nc)); L[9] = d2f(0.5 * (-b1u + ic)); L[10] = d2f(hb1); L[11] = 0.f;
         L[12] = L[13] = L[14] = L[15] = 0.f;
       } else {
         const double x0 = dir == 0 ? -ic : 0.0, y0 = dir == 0 ? 0.0 : -ic;
-        L[0] = (float)(0.5 * (b2 + nc)); L[1] = (float)(0.5 * (-b1u + x0)); L[2] = (float)(0.5 * (-b1v + y0));
-        L[3] = (float)hb1;
-        L[4] = (float)(1.0 - b2); L[5] = (float)b1u; L[6] = (float)b1v; L[7] = (float)(-b1);
-        L[8] = (float)(dir == 0 ? -vt : -ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
+        L[0] = d2f(0.5 * (b2 + nc)); L[1] = d2f(0.5 * (-b1u + x0)); L[2] = d2f(0.5 * (-b1v + y0));
+        L[3] = d2f(hb1);
+        L[4] = d2f(1.0 - b2); L[5] = d2f(b1u); L[6] = d2f(b1v); L[7] = d2f(-b1);
+        L[8] = d2f(dir == 0 ? -vt : -ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
         L[11] = 0.f;
-        L[12] = (float)(0.5 * (b2 - nc)); L[13] = (float)(0.5 * (-b1u - x0)); L[14] = (float)(0.5 * (-b1v - y0));
-        L[15] = (float)hb1;
+        L[12] = d2f(0.5 * (b2 - nc)); L[13] = d2f(0.5 * (-b1u - x0)); L[14] = d2f(0.5 * (-b1v - y0));
+        L[15] = d2f(hb1);
       }
       float* R = sRf + k * 5;
-      R[0] = (float)ut; R[1] = (float)vt; R[2] = (float)Ht; R[3] = (float)ct; R[4] = (float)qt;
+      R[0] = d2f(ut); R[1] = d2f(vt); R[2] = d2f(Ht); R[3] = d2f(ct); R[4] = d2f(qt);
     }
     __syncthreads();
     // ---- four tensor-core batches of 16 faces x 4 fields x 2 sides
@@ -407,7 +459,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
         corr = fmaf(R1, ghq[1], corr);
         corr = fmaf(R2, ghq[2], corr);
         if (NDIM == 2) corr = fmaf(R3, ghq[3], corr);
-        const double Fh = refd[4 + n] + (double)corr;
+        const double Fh = refd[4 + n] + f2d(corr);
         size_t idx;
         if (dir == 0) {
           const int f = f0 + k;

@@ -42,6 +42,7 @@ struct MlpCtx {
   uint32_t tmem;
   uint32_t phase;
   bool bf16;
+  int* fail;           // shared timeout flag
 };
 
 // Issue one layer (thread 0): ksteps MMAs of K = 16 into TMEM column `col`.
@@ -57,20 +58,23 @@ __device__ __forceinline__ void issue_layer(const MlpCtx& c, const uint8_t* A, i
   mma_commit(c.bar);
 }
 
-// Wait for the layer's MMAs; false on timeout (uniform across the CTA).
-__device__ __forceinline__ bool wait_layer(MlpCtx& c) {
-  const bool ok = mbar_wait(c.bar, c.phase);
+// Wait for the layer's MMAs (bounded).  A timeout is recorded in the shared
+// flag *fail and acted on, uniformly, at the end of the chain.
+__device__ __forceinline__ void wait_layer(MlpCtx& c) {
+  if (!mbar_wait(c.bar, c.phase)) *c.fail = 1;
   c.phase ^= 1u;
   tc_fence_after();
-  return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// Epilogue of a hidden layer: acc(row) + bias -> ReLU -> 16-bit -> next A.
+// Epilogue of a hidden tensor-core layer: acc(row) + bias -> ReLU -> 16-bit
+// -> this row of the next layer's operand.
 template <int N>
 __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bias_off, uint8_t* Anext) {
   const int t = threadIdx.x;
   const uint32_t lane = (uint32_t)(t & ~31) << 16;
   const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias) + bias_off;
+  // fp16 activations are kept below the fp16 maximum
+  const float hi = c.bf16 ? 3.0e38f : 65000.0f;
 #pragma unroll
   for (int c16 = 0; c16 < N / 16; ++c16) {
     uint32_t r[16];
@@ -79,8 +83,6 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bi
     uint32_t p[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      // ReLU; fp16 activations are also kept below the fp16 maximum
-      const float hi = c.bf16 ? 3.0e38f : 65000.0f;
       const float a = fminf(fmaxf(__uint_as_float(r[2 * i]) + bias[16 * c16 + 2 * i], 0.0f), hi);
       const float b = fminf(fmaxf(__uint_as_float(r[2 * i + 1]) + bias[16 * c16 + 2 * i + 1], 0.0f), hi);
       p[i] = pack2(a, b, c.bf16);
@@ -93,32 +95,47 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bi
   __syncthreads();
 }
 
-// Layers 1..5 for the 128 rows whose layer-1 inputs are in bufY (K = 16).
-// Returns false on an MMA timeout.
+// The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16):
+// layers 1-3 on the tensor cores (TMEM columns [0,64), [64,96), [96,112)),
+// layers 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores from layer 3's
+// accumulator row.  Returns false (uniformly) if an MMA wait timed out.
 __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
   if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB1, 64, 0);
-  if (!wait_layer(c)) return false;
+  wait_layer(c);
   hidden_epilogue<64>(c, 0, 0, c.bufX);
   if (threadIdx.x == 0) issue_layer(c, c.bufX, 64, kNetImageB2, 32, 64);
-  if (!wait_layer(c)) return false;
+  wait_layer(c);
   hidden_epilogue<32>(c, 64, 64, c.bufY);
   if (threadIdx.x == 0) issue_layer(c, c.bufY, 32, kNetImageB3, 16, 96);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<16>(c, 96, 96, c.bufX);
-  if (threadIdx.x == 0) issue_layer(c, c.bufX, 16, kNetImageB4, 16, 112);
-  if (!wait_layer(c)) return false;
-  hidden_epilogue<16>(c, 112, 112, c.bufY);
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB5, 16, 0);
-  if (!wait_layer(c)) return false;
+  wait_layer(c);
   const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
   uint32_t r[16];
-  tmem_ld16(c.tmem + lane, r);
+  tmem_ld16(c.tmem + lane + 96u, r);
   tmem_ld_wait();
-  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias) + 128;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) z[k] = __uint_as_float(r[k]) + bias[k];
   tc_fence_before();
-  return true;
+  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
+  const float* W4 = reinterpret_cast<const float*>(c.net + kNetImageW4);
+  const float* W5 = reinterpret_cast<const float*>(c.net + kNetImageW5);
+  float h3[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) h3[i] = fmaxf(__uint_as_float(r[i]) + bias[96 + i], 0.0f);
+  float h4[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float a = bias[112 + o];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a = fmaf(W4[o * 16 + i], h3[i], a);
+    h4[o] = fmaxf(a, 0.0f);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float a = bias[120 + k];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a = fmaf(W5[k * 8 + i], h4[i], a);
+    z[k] = a;
+  }
+  // every thread's timeout record is visible after this barrier
+  return __syncthreads_or(*c.fail) == 0;
 }
 
 // Copy the classifier image (16-byte chunks) into shared memory.
