@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
     s_fail = 0;
   }
   if (t < 32) {
-    tmem_alloc(&s_tmem, 128);
+    tmem_alloc(&s_tmem, 64);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (t < 32) tmem_dealloc(s_tmem, 128);
+  if (t < 32) tmem_dealloc(s_tmem, 64);
 }
 
 // Round a binary64 value to the nearest bf16 (ties to even) in one step.

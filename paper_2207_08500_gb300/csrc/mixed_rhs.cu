@@ -14,8 +14,8 @@
 //         rows whose logits fall within +-guard_tau of 0 re-evaluated in FP32
 //         on the CUDA cores.
 //
-// Face kernel: persistent CTAs of one warpgroup (up to four per SM, each with
-// 128 TMEM columns).  A block is 64 faces — 64 consecutive x faces of one
+// Face kernel: persistent CTAs of one warpgroup (five per SM, each with 64
+// TMEM columns).  A block is 64 faces — 64 consecutive x faces of one
 // row, or 4 columns x 16 consecutive y faces.  Per block: stage the stencil
 // cells (ghost cells by wrap / clamp), compute the 64 Roe states once (one
 // thread per face, FP64), then four 128-row tensor-core batches of 16 faces x
@@ -60,8 +60,9 @@ constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8); // 10 x kMaxC
 constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16 floats
 constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 floats
 constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
-constexpr int kOffGuard = align_up(kOffRef + 8 * 8 + 8 * 4);      // 4 warps x 128 floats
-constexpr int kOffBar = align_up(kOffGuard + 4 * 128 * 4);
+// the guard band's per-warp scratch (4 x 128 floats) reuses the layer-2
+// operand buffer, which is free once a batch's MMAs are done
+constexpr int kOffBar = align_up(kOffRef + 8 * 8 + 8 * 4);
 constexpr int kFacesSmem = kOffBar + 16;
 
 // per-cell arrays
@@ -180,14 +181,14 @@ __device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* w
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
+__global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_net = smem + kOffNet;
   double* cd = reinterpret_cast<double*>(smem + kOffCellD);
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
-  float* ws = reinterpret_cast<float*>(smem + kOffGuard) + (threadIdx.x >> 5) * 128;
+  float* ws = reinterpret_cast<float*>(smem + kOffBufX) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
   int* fail_flag = reinterpret_cast<int*>(smem + kOffBar + 12);
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
     *fail_flag = 0;
   }
   if (t < 32) {
-    tmem_alloc(tmem_slot, 128);
+    tmem_alloc(tmem_slot, 64);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(kMlpThreads, 4) faces_mixed_kernel(const __gri
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (t < 32) tmem_dealloc(*tmem_slot, 128);
+  if (t < 32) tmem_dealloc(*tmem_slot, 64);
 }
 
 // Conservative difference (FP64) and optional SSP-RK3 stage update.
@@ -549,7 +550,9 @@ cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
   a.byc = (a.nx + kYCols - 1) / kYCols;
   a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kYFaces - 1) / kYFaces) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
-  const int blocks = (int)(nblk < 152 * 4 ? nblk : 152 * 4);
+  // persistent grid: five resident CTAs per SM (registers, shared memory,
+  // 64 TMEM columns each)
+  const int blocks = (int)(nblk < 152 * 5 ? nblk : 152 * 5);
   cudaError_t e;
   if (ndim == 2) {
     e = cudaFuncSetAttribute(faces_mixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);

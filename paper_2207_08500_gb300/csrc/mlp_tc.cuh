@@ -95,22 +95,12 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bi
   __syncthreads();
 }
 
-// The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16):
-// layers 1-3 on the tensor cores (TMEM columns [0,64), [64,96), [96,112)),
-// layers 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores from layer 3's
-// accumulator row.  Returns false (uniformly) if an MMA wait timed out.
-__device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB1, 64, 0);
-  wait_layer(c);
-  hidden_epilogue<64>(c, 0, 0, c.bufX);
-  if (threadIdx.x == 0) issue_layer(c, c.bufX, 64, kNetImageB2, 32, 64);
-  wait_layer(c);
-  hidden_epilogue<32>(c, 64, 64, c.bufY);
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 32, kNetImageB3, 16, 96);
-  wait_layer(c);
+// Layer 3's accumulator row (TMEM column col) + bias -> ReLU, then layers
+// 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores.
+__device__ __forceinline__ void tail_layers(const MlpCtx& c, int col, float z[4]) {
   const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
   uint32_t r[16];
-  tmem_ld16(c.tmem + lane + 96u, r);
+  tmem_ld16(c.tmem + lane + (uint32_t)col, r);
   tmem_ld_wait();
   tc_fence_before();
   const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
@@ -134,6 +124,24 @@ __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
     for (int i = 0; i < 8; ++i) a = fmaf(W5[k * 8 + i], h4[i], a);
     z[k] = a;
   }
+}
+
+// The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16):
+// layers 1-3 on the tensor cores, layers 4-5 on the CUDA cores.  64 TMEM
+// columns: layer 1 -> [0,64); layer 2 -> [0,32) once layer 1's epilogue has
+// read its columns (the epilogue ends with a fence and a barrier before the
+// next issue); layer 3 -> [32,48).  Returns false (uniformly) if an MMA wait
+// timed out.
+__device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
+  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB1, 64, 0);
+  wait_layer(c);
+  hidden_epilogue<64>(c, 0, 0, c.bufX);
+  if (threadIdx.x == 0) issue_layer(c, c.bufX, 64, kNetImageB2, 32, 0);
+  wait_layer(c);
+  hidden_epilogue<32>(c, 0, 64, c.bufY);
+  if (threadIdx.x == 0) issue_layer(c, c.bufY, 32, kNetImageB3, 16, 32);
+  wait_layer(c);
+  tail_layers(c, 32, z);
   // every thread's timeout record is visible after this barrier
   return __syncthreads_or(*c.fail) == 0;
 }
