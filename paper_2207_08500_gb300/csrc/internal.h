@@ -57,14 +57,21 @@ struct ClassifyParamsF64 {
 
 // Tensor-core image of the classifier (mixed precision): layers 1-3 as 16-bit
 // B operands W_l[out][in] in the K-major canonical layout (K of layer 1
-// padded 6 -> 16), then all FP32 biases (b1 at 0, b2 at 64, b3 at 96, b4 at
-// 112, b5 at 120), then the FP32 weights of layers 4 and 5 (W4[8][16],
-// W5[4][8]), which run on the CUDA cores.
-constexpr int kNetImageB1 = 0;                          // 64 x 16
-constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;  // 32 x 64
-constexpr int kNetImageB3 = kNetImageB2 + 32 * 64 * 2;  // 16 x 32
+// padded 6 -> 16).  The biases of layers 1 and 2 ride on the tensor cores:
+// the layer-1 input row carries 1 in columns kOnesCol..kOnesCol+2, B1 holds
+// b1 split into three 16-bit terms (hi + mid + lo, ~24 significant bits) in
+// those columns, and a fifth K-step of layer 2 multiplies the same input tile
+// by the 32 x 16 tile B2b that holds b2's three terms in those columns (zero
+// elsewhere).  Then the FP32 biases of layers 3-5 (b3 at 0, b4 at 16, b5 at
+// 24) and the FP32 weights of layers 4 and 5, stored transposed
+// (W4^T[16][8], W5^T[8][4]) for packed two-output FMAs on the CUDA cores.
+constexpr int kOnesCol = 6;
+constexpr int kNetImageB1 = 0;                           // 64 x 16
+constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;   // 32 x 64
+constexpr int kNetImageB2b = kNetImageB2 + 32 * 64 * 2;  // 32 x 16
+constexpr int kNetImageB3 = kNetImageB2b + 32 * 16 * 2;  // 16 x 32
 constexpr int kNetImageBias = kNetImageB3 + 16 * 32 * 2;
-constexpr int kNetImageW4 = kNetImageBias + 128 * 4;
+constexpr int kNetImageW4 = kNetImageBias + 32 * 4;
 constexpr int kNetImageW5 = kNetImageW4 + 8 * 16 * 4;
 constexpr int kNetImageBytes = kNetImageW5 + 4 * 8 * 4;
 static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");

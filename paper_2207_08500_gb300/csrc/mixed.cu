@@ -6,12 +6,13 @@
 // Tensor-core MLP (one warpgroup per CTA): thread t owns row t of a 128-row
 // batch, which is TMEM lane t and MMA row t.  Layer l's input (128 x K_l, K
 // padded to a multiple of 16) sits in shared memory in the K-major canonical
-// layout of tc.cuh; thread 0 issues the MMAs (D = A * W^T, N = layer width
-// padded to 16) and commits them to an mbarrier; every thread waits (bounded),
-// loads its row of the FP32 accumulator from TMEM, adds the FP32 bias, applies
-// ReLU, rounds to bf16/fp16 and stores it as its row of the next layer's
-// input.  TMEM columns: layer 1 [0,64), 2 [64,96), 3 [96,112), 4 [112,128),
-// 5 [0,16) — 128 columns per CTA, so up to four CTAs share an SM.
+// layout of tc.cuh; thread 0 issues the MMAs (D = A * W^T, N = layer width)
+// and commits them to an mbarrier; every thread waits (bounded), loads its
+// row of the FP32 accumulator from TMEM, applies ReLU, rounds to bf16/fp16
+// (one packed cvt per pair) and stores it as its row of the next layer's
+// input.  The biases of layers 1 and 2 are accumulated by the tensor cores
+// (constant-one input columns, see kOnesCol); layer 3's bias and layers 4-5
+// (16 -> 8 -> 4) run in FP32 on the CUDA cores.  64 TMEM columns per CTA.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -31,11 +32,12 @@ using namespace tcmlp;
 // Batched classifier (neno6_classify, mixed precision): persistent CTAs of
 // 128 threads, one 128-row tile per iteration.  Normalisation (Eq.
 // (normalizainput)) in FP32, then the tensor-core MLP; logit > 0 -> discard.
+template <bool BF16>
 __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const double* __restrict__ X,
                                                                       long long n, uint8_t* __restrict__ eta,
                                                                       double* __restrict__ logits,
                                                                       const uint8_t* __restrict__ net_image,
-                                                                      int bf16, int* status) {
+                                                                      int* status) {
   __shared__ __align__(128) uint8_t s_net[kNetImageBytes];
   __shared__ __align__(128) uint8_t s_bufX[kBufXBytes];
   __shared__ __align__(128) uint8_t s_bufY[kBufYBytes];
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx c{s_net, s_bufX, s_bufY, &s_bar, s_tmem, 0u, bf16 != 0, &s_fail};
+  MlpCtx c{s_net, s_bufX, s_bufY, &s_bar, s_tmem, 0u, BF16, &s_fail};
   const long long tiles = (n + 127) / 128;
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long r = tile * 128 + t;
@@ -69,12 +71,11 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
     }
 #pragma unroll
     for (int j = 0; j < 6; ++j) x[j] = x[j] / m;
-    st_row8(s_bufY, t, 0, 16, pack2(x[0], x[1], c.bf16), pack2(x[2], x[3], c.bf16), pack2(x[4], x[5], c.bf16), 0u);
-    st_row8(s_bufY, t, 8, 16, 0u, 0u, 0u, 0u);
+    store_input_row<BF16>(s_bufY, t, x);
     fence_async_smem();
     __syncthreads();
     float z[4];
-    if (!mlp_tc(c, z)) {
+    if (!mlp_tc<BF16>(c, z)) {
       if (t == 0) atomicOr(status, 4);
       break;
     }
@@ -116,34 +117,58 @@ uint16_t to_fp16_bits(double d) {
   return u;
 }
 
+double from_16_bits(uint16_t b, bool bf16) {
+  if (bf16) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+  }
+  __half h;
+  std::memcpy(&h, &b, 2);
+  return (double)__half2float(h);
+}
+
 }  // namespace
 
 // Host: lay the FP64 master parameters out as the tensor-core image.
 void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
   std::memset(img, 0, kNetImageBytes);
-  auto put = [&](int off, int K, int n, int k, double w) {
-    const uint16_t b = bf16 ? to_bf16_bits(w) : to_fp16_bits(w);
+  auto bits = [&](double w) { return bf16 ? to_bf16_bits(w) : to_fp16_bits(w); };
+  auto put_bits = [&](int off, int K, int n, int k, uint16_t b) {
     std::memcpy(img + off + kmajor_offset(n, k, K), &b, 2);
+  };
+  // b = hi + mid + lo, each term the 16-bit rounding of what is left
+  auto put_bias = [&](int off, int K, int n, double b) {
+    for (int q = 0; q < 3; ++q) {
+      const uint16_t h = bits(b);
+      put_bits(off, K, n, kOnesCol + q, h);
+      b -= from_16_bits(h, bf16);
+    }
   };
   const int widths[6] = {6, 64, 32, 16, 8, 4};
   const int boff[3] = {kNetImageB1, kNetImageB2, kNetImageB3};
   const int Kpad[3] = {16, 64, 32};
-  const int bias_off[5] = {0, 64, 96, 112, 120};
   float* bias = reinterpret_cast<float*>(img + kNetImageBias);
-  float* w4 = reinterpret_cast<float*>(img + kNetImageW4);
-  float* w5 = reinterpret_cast<float*>(img + kNetImageW5);
+  float* w4t = reinterpret_cast<float*>(img + kNetImageW4);
+  float* w5t = reinterpret_cast<float*>(img + kNetImageW5);
   size_t p = 0;
   for (int l = 0; l < 5; ++l) {
     const int nin = widths[l], nout = widths[l + 1];
     for (int o = 0; o < nout; ++o)
       for (int i = 0; i < nin; ++i) {
         const double w = net.p[p + (size_t)o * nin + i];
-        if (l < 3) put(boff[l], Kpad[l], o, i, w);
-        else if (l == 3) w4[o * 16 + i] = (float)w;
-        else w5[o * 8 + i] = (float)w;
+        if (l < 3) put_bits(boff[l], Kpad[l], o, i, bits(w));
+        else if (l == 3) w4t[i * 8 + o] = (float)w;
+        else w5t[i * 4 + o] = (float)w;
       }
     p += (size_t)nout * nin;
-    for (int o = 0; o < nout; ++o) bias[bias_off[l] + o] = (float)net.p[p + o];
+    for (int o = 0; o < nout; ++o) {
+      const double b = net.p[p + o];
+      if (l == 0) put_bias(kNetImageB1, 16, o, b);
+      else if (l == 1) put_bias(kNetImageB2b, 16, o, b);
+      else bias[(l == 2 ? 0 : l == 3 ? 16 : 24) + o] = (float)b;
+    }
     p += nout;
   }
 }
@@ -152,14 +177,14 @@ cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, do
                                   const uint8_t* net_image, bool bf16, int* status, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const long long tiles = (n + 127) / 128;
-  const int blocks = (int)(tiles < 152 * 4 ? tiles : 152 * 4);
-  // 16 KB of unused dynamic shared memory keeps residency at <= 4 CTAs per
-  // SM, so the four 128-column TMEM allocations always fit.
-  constexpr int kPadSmem = 16 * 1024;
-  cudaError_t e = cudaFuncSetAttribute(classify_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPadSmem);
-  if (e != cudaSuccess) return e;
-  classify_mixed_kernel<<<blocks, kMlpThreads, kPadSmem, s>>>(X, n, eta, logits, net_image, bf16 ? 1 : 0,
-                                                              status);
+  // the static shared memory (~35 KB with the per-CTA reserve) caps
+  // residency at six CTAs of the SM's 228 KB, so their 64-column TMEM
+  // allocations always fit in the 512 columns
+  static_assert(kNetImageBytes + kBufXBytes + kBufYBytes + 1024 > 228 * 1024 / 9,
+                "nine resident CTAs would oversubscribe TMEM");
+  const int blocks = (int)(tiles < 152 * 6 ? tiles : 152 * 6);
+  if (bf16) classify_mixed_kernel<true><<<blocks, kMlpThreads, 0, s>>>(X, n, eta, logits, net_image, status);
+  else classify_mixed_kernel<false><<<blocks, kMlpThreads, 0, s>>>(X, n, eta, logits, net_image, status);
   return cudaGetLastError();
 }
 

@@ -56,18 +56,23 @@ constexpr int kOffNet = 0;
 constexpr int kOffBufX = align_up(kOffNet + kNetImageBytes);
 constexpr int kOffBufY = align_up(kOffBufX + kBufXBytes);
 constexpr int kOffCellD = align_up(kOffBufY + kBufYBytes);      // 4 x kMaxCells doubles
-constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8); // 10 x kMaxCells floats
+// per cell 8 floats (U_n, F_n deviations interleaved), then per cell 2 floats
+// (normal velocity, sound speed)
+constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8);
 constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16 floats
 constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 floats
 constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
+constexpr int kOffBar = kOffRef + 8 * 8 + 8 * 4;  // mbarrier, TMEM address, timeout flag
+constexpr int kFacesSmem = align_up(kOffBar + 16);
 // the guard band's per-warp scratch (4 x 128 floats) reuses the layer-2
-// operand buffer, which is free once a batch's MMAs are done
-constexpr int kOffBar = align_up(kOffRef + 8 * 8 + 8 * 4);
-constexpr int kFacesSmem = kOffBar + 16;
+// operand buffer, which is free once a batch's MMAs are done.
+// Five CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
+// plus 1 KB reserved per CTA.
+static_assert(kOffBar % 8 == 0 && kFacesSmem % 128 == 0, "alignment");
+static_assert(5 * (kFacesSmem + 1024) <= 228 * 1024, "face kernel: five CTAs per SM");
 
 // per-cell arrays
 enum { CD_S = 0, CD_U = 1, CD_V = 2, CD_H = 3 };
-enum { CF_U = 0, CF_F = 4, CF_UN = 8, CF_C = 9 };
 
 __device__ __forceinline__ int wrap_idx(int i, int n, int bc) {
   if (bc == 0) {
@@ -180,13 +185,14 @@ __device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* w
   }
 }
 
-template <int NDIM>
+template <int NDIM, bool BF16>
 __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_net = smem + kOffNet;
   double* cd = reinterpret_cast<double*>(smem + kOffCellD);
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
+  float2* cuc = reinterpret_cast<float2*>(cf + 8 * kMaxCells);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
   float* ws = reinterpret_cast<float*>(smem + kOffBufX) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, a.bf16 != 0, fail_flag};
+  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, BF16, fail_flag};
   unsigned long long guarded = 0;
   bool failed = false;
 
@@ -274,8 +280,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       } else {
         F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
       }
-      cf[CF_UN * kMaxCells + tr] = d2f(dir == 0 ? u : v);
-      cf[CF_C * kMaxCells + tr] = sqrtf(gamma_f * d2f(p) * d2f(rr));
+      cuc[tr] = make_float2(d2f(dir == 0 ? u : v), sqrtf(gamma_f * d2f(p) * d2f(rr)));
       if (tr == 0) {  // the block's reference state
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
@@ -289,11 +294,15 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
     __syncthreads();
     // ---- deviations from the reference, rounded to FP32
     if (tr < ncells) {
+      float w[8];
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
-        cf[(CF_U + n) * kMaxCells + tr] = n < NV ? d2f(U[n] - refd[n]) : 0.0f;
-        cf[(CF_F + n) * kMaxCells + tr] = d2f(F[n] - refd[4 + n]);
+        w[2 * n] = n < NV ? d2f(U[n] - refd[n]) : 0.0f;
+        w[2 * n + 1] = d2f(F[n] - refd[4 + n]);
       }
+      float4* dst = reinterpret_cast<float4*>(cf + 8 * tr);
+      dst[0] = make_float4(w[0], w[1], w[2], w[3]);
+      dst[1] = make_float4(w[4], w[5], w[6], w[7]);
     }
     // ---- Roe average and eigenvectors (FP64), one thread per face
     const int tq = (tr + 64) & (kMlpThreads - 1);  // the other half of the CTA
@@ -345,13 +354,13 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
       const bool valid = fld < NV &&
                          (dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx));
-      const float* Lr = sL + k * 16 + m * 4;
+      const float4 Lv = *reinterpret_cast<const float4*>(sL + k * 16 + m * 4);
+      const float Lr[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
       float alpha = 0.0f;
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        const int cj = cb0 + j * cstride;
-        const float un = cf[CF_UN * kMaxCells + cj], cs = cf[CF_C * kMaxCells + cj];
-        const float lam = m == 0 ? un - cs : (m == NV - 1 ? un + cs : un);
+        const float2 uc = cuc[cb0 + j * cstride];
+        const float lam = m == 0 ? uc.x - uc.y : (m == NV - 1 ? uc.x + uc.y : uc.x);
         alpha = fmaxf(alpha, fabsf(lam));
       }
       const float sgn_alpha = side ? -alpha : alpha;
@@ -366,15 +375,14 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       float ds[6];  // deviations of the split flux from the reference part
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        const int cj = cb0 + j * cstride;
-        float vv = Lr[0] * cf[(CF_U + 0) * kMaxCells + cj];
-        float gg = Lr[0] * cf[(CF_F + 0) * kMaxCells + cj];
-#pragma unroll
-        for (int n = 1; n < NV; ++n) {
-          vv = fmaf(Lr[n], cf[(CF_U + n) * kMaxCells + cj], vv);
-          gg = fmaf(Lr[n], cf[(CF_F + n) * kMaxCells + cj], gg);
-        }
-        const float val = 0.5f * fmaf(sgn_alpha, vv, gg);
+        // (v, g) = L_m . (U_j, F_j) deviations, both in one packed FMA chain
+        const float4* src = reinterpret_cast<const float4*>(cf + 8 * (cb0 + j * cstride));
+        const float4 p0 = src[0], p1 = src[1];
+        float2 vg = __fmul2_rn(make_float2(Lr[0], Lr[0]), make_float2(p0.x, p0.y));
+        vg = __ffma2_rn(make_float2(Lr[1], Lr[1]), make_float2(p0.z, p0.w), vg);
+        vg = __ffma2_rn(make_float2(Lr[2], Lr[2]), make_float2(p1.x, p1.y), vg);
+        if (NV == 4) vg = __ffma2_rn(make_float2(Lr[3], Lr[3]), make_float2(p1.z, p1.w), vg);
+        const float val = 0.5f * fmaf(sgn_alpha, vg.x, vg.y);
         // "+" side: stencil i-2..i+3; "-" side: its mirror image
         if (side == 0) ds[j] = val;
         else ds[5 - j] = val;
@@ -391,13 +399,11 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       for (int j = 0; j < 6; ++j) x[j] = s[j] * inv;
       unsigned eta;
       if (a.mask_mode == kMaskMLP) {
-        st_row8(mc.bufY, t, 0, 16, pack2(x[0], x[1], mc.bf16), pack2(x[2], x[3], mc.bf16),
-                pack2(x[4], x[5], mc.bf16), 0u);
-        st_row8(mc.bufY, t, 8, 16, 0u, 0u, 0u, 0u);
+        store_input_row<BF16>(mc.bufY, t, x);
         fence_async_smem();
         __syncthreads();
         float z[4];
-        if (!mlp_tc(mc, z)) {
+        if (!mlp_tc<BF16>(mc, z)) {
           failed = true;
           break;
         }
@@ -553,16 +559,11 @@ cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
   // persistent grid: five resident CTAs per SM (registers, shared memory,
   // 64 TMEM columns each)
   const int blocks = (int)(nblk < 152 * 5 ? nblk : 152 * 5);
-  cudaError_t e;
-  if (ndim == 2) {
-    e = cudaFuncSetAttribute(faces_mixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);
-    if (e != cudaSuccess) return e;
-    faces_mixed_kernel<2><<<blocks, kMlpThreads, kFacesSmem, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(faces_mixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);
-    if (e != cudaSuccess) return e;
-    faces_mixed_kernel<1><<<blocks, kMlpThreads, kFacesSmem, s>>>(a);
-  }
+  auto kern = ndim == 2 ? (a.bf16 ? faces_mixed_kernel<2, true> : faces_mixed_kernel<2, false>)
+                        : (a.bf16 ? faces_mixed_kernel<1, true> : faces_mixed_kernel<1, false>);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, kMlpThreads, kFacesSmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -17,8 +17,10 @@ constexpr int kMlpThreads = 128;
 constexpr int kBufXBytes = 128 * 64 * 2;  // A2 (K = 64) / A4
 constexpr int kBufYBytes = 128 * 32 * 2;  // A1 / A3 (K = 32) / A5
 
-__device__ __forceinline__ uint32_t pack2(float a, float b, bool bf16) {
-  if (bf16) {
+// Round two FP32 values to bf16/fp16 and pack them, a in bits 0-15.
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if (BF16) {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&v);
   }
@@ -26,12 +28,42 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, bool bf16) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// ReLU, round to the nearest finite 16-bit value and pack (a in bits 0-15):
+// one cvt instruction per pair.  Saturating to the largest finite value keeps
+// fp16 activations finite.
+template <bool BF16>
+__device__ __forceinline__ uint32_t relu_pack2(float a, float b) {
+  uint32_t d;
+  if (BF16)
+    asm("cvt.rn.relu.satfinite.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  else
+    asm("cvt.rn.relu.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
+
+// The 16-bit pair (1, 1) and (1, 0): the constant columns of the layer-1
+// input row that carry the biases of layers 1 and 2.
+template <bool BF16>
+__device__ __forceinline__ constexpr uint32_t ones2() { return BF16 ? 0x3F803F80u : 0x3C003C00u; }
+template <bool BF16>
+__device__ __forceinline__ constexpr uint32_t one0() { return BF16 ? 0x00003F80u : 0x00003C00u; }
+
 // Store 8 consecutive K values (one core-matrix row) of row `row`.
 __device__ __forceinline__ void st_row8(uint8_t* base, int row, int k0, int K, uint32_t a, uint32_t b,
                                         uint32_t c, uint32_t d) {
   const uint32_t addr = smem_u32(base + kmajor_offset(row, k0, K));
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
                : "memory");
+}
+
+// Row `row` of the layer-1 input tile (K = 16): the six normalised stencil
+// values, then 1, 1, 1 in columns kOnesCol..kOnesCol+2 (bias terms), zeros.
+template <bool BF16>
+__device__ __forceinline__ void store_input_row(uint8_t* bufY, int row, const float x[6]) {
+  static_assert(kOnesCol == 6, "ones occupy columns 6-8");
+  st_row8(bufY, row, 0, 16, pack2<BF16>(x[0], x[1]), pack2<BF16>(x[2], x[3]), pack2<BF16>(x[4], x[5]),
+          ones2<BF16>());
+  st_row8(bufY, row, 8, 16, one0<BF16>(), 0u, 0u, 0u);
 }
 
 struct MlpCtx {
@@ -45,16 +77,22 @@ struct MlpCtx {
   int* fail;           // shared timeout flag
 };
 
-// Issue one layer (thread 0): ksteps MMAs of K = 16 into TMEM column `col`.
+// Issue one layer (thread 0): K/16 MMAs of K = 16 into TMEM column `col`,
+// plus, if Bb_off >= 0, a bias K-step (the layer-1 input tile in bufY, whose
+// columns 6-8 hold 1, times the bias tile at Bb_off).
+template <bool BF16>
 __device__ __forceinline__ void issue_layer(const MlpCtx& c, const uint8_t* A, int K, int B_off, int N,
-                                            int col) {
+                                            int col, int Bb_off = -1) {
   const uint32_t sbo = (uint32_t)(K / 8) * 128u;
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(c.net + B_off);
-  const uint32_t idesc = idesc_f16(128, N, c.bf16);
+  const uint32_t idesc = idesc_f16(128, N, BF16);
   tc_fence_after();
   for (int ks = 0; ks < K / 16; ++ks)
     mma_f16(c.tmem + (uint32_t)col, smem_desc(a0 + 256u * ks, 128u, sbo),
             smem_desc(b0 + 256u * ks, 128u, sbo), idesc, ks > 0 ? 1u : 0u);
+  if (Bb_off >= 0)
+    mma_f16(c.tmem + (uint32_t)col, smem_desc(smem_u32(c.bufY), 128u, 256u),
+            smem_desc(smem_u32(c.net + Bb_off), 128u, 256u), idesc, 1u);
   mma_commit(c.bar);
 }
 
@@ -66,29 +104,28 @@ __device__ __forceinline__ void wait_layer(MlpCtx& c) {
   tc_fence_after();
 }
 
-// Epilogue of a hidden tensor-core layer: acc(row) + bias -> ReLU -> 16-bit
-// -> this row of the next layer's operand.
-template <int N>
-__device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bias_off, uint8_t* Anext) {
+// Epilogue of a hidden tensor-core layer (bias already accumulated): this
+// row of the FP32 accumulator -> ReLU -> 16-bit -> this row of the next
+// layer's operand, 32 columns per TMEM round trip.
+template <int N, bool BF16>
+__device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, uint8_t* Anext) {
   const int t = threadIdx.x;
   const uint32_t lane = (uint32_t)(t & ~31) << 16;
-  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias) + bias_off;
-  // fp16 activations are kept below the fp16 maximum
-  const float hi = c.bf16 ? 3.0e38f : 65000.0f;
 #pragma unroll
-  for (int c16 = 0; c16 < N / 16; ++c16) {
-    uint32_t r[16];
-    tmem_ld16(c.tmem + lane + (uint32_t)(col + 16 * c16), r);
+  for (int c32 = 0; c32 < N / 32; ++c32) {
+    uint32_t r[16], s[16];
+    tmem_ld16(c.tmem + lane + (uint32_t)(col + 32 * c32), r);
+    tmem_ld16(c.tmem + lane + (uint32_t)(col + 32 * c32 + 16), s);
     tmem_ld_wait();
-    uint32_t p[8];
+    uint32_t p[16];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float a = fminf(fmaxf(__uint_as_float(r[2 * i]) + bias[16 * c16 + 2 * i], 0.0f), hi);
-      const float b = fminf(fmaxf(__uint_as_float(r[2 * i + 1]) + bias[16 * c16 + 2 * i + 1], 0.0f), hi);
-      p[i] = pack2(a, b, c.bf16);
+      p[i] = relu_pack2<BF16>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+      p[8 + i] = relu_pack2<BF16>(__uint_as_float(s[2 * i]), __uint_as_float(s[2 * i + 1]));
     }
-    st_row8(Anext, t, 16 * c16, N, p[0], p[1], p[2], p[3]);
-    st_row8(Anext, t, 16 * c16 + 8, N, p[4], p[5], p[6], p[7]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      st_row8(Anext, t, 32 * c32 + 8 * q, N, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
   }
   tc_fence_before();
   fence_async_smem();
@@ -96,7 +133,9 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, int bi
 }
 
 // Layer 3's accumulator row (TMEM column col) + bias -> ReLU, then layers
-// 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores.
+// 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores, two outputs per packed FMA
+// (each output still accumulates over its inputs in order, one rounding per
+// FMA).
 __device__ __forceinline__ void tail_layers(const MlpCtx& c, int col, float z[4]) {
   const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
   uint32_t r[16];
@@ -104,42 +143,58 @@ __device__ __forceinline__ void tail_layers(const MlpCtx& c, int col, float z[4]
   tmem_ld_wait();
   tc_fence_before();
   const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
-  const float* W4 = reinterpret_cast<const float*>(c.net + kNetImageW4);
-  const float* W5 = reinterpret_cast<const float*>(c.net + kNetImageW5);
+  const float2* W4t = reinterpret_cast<const float2*>(c.net + kNetImageW4);  // [16][4] pairs
+  const float2* W5t = reinterpret_cast<const float2*>(c.net + kNetImageW5);  // [8][2] pairs
   float h3[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) h3[i] = fmaxf(__uint_as_float(r[i]) + bias[96 + i], 0.0f);
+  for (int i = 0; i < 16; ++i) h3[i] = fmaxf(__uint_as_float(r[i]) + bias[i], 0.0f);
+  float2 a4[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) a4[o] = reinterpret_cast<const float2*>(bias + 16)[o];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float2 h = make_float2(h3[i], h3[i]);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) a4[o] = __ffma2_rn(W4t[i * 4 + o], h, a4[o]);
+  }
   float h4[8];
 #pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    float a = bias[112 + o];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) a = fmaf(W4[o * 16 + i], h3[i], a);
-    h4[o] = fmaxf(a, 0.0f);
+  for (int o = 0; o < 4; ++o) {
+    h4[2 * o] = fmaxf(a4[o].x, 0.0f);
+    h4[2 * o + 1] = fmaxf(a4[o].y, 0.0f);
   }
+  float2 a5[2];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float a = bias[120 + k];
+  for (int k = 0; k < 2; ++k) a5[k] = reinterpret_cast<const float2*>(bias + 24)[k];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a = fmaf(W5[k * 8 + i], h4[i], a);
-    z[k] = a;
+  for (int i = 0; i < 8; ++i) {
+    const float2 h = make_float2(h4[i], h4[i]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) a5[k] = __ffma2_rn(W5t[i * 2 + k], h, a5[k]);
   }
+  z[0] = a5[0].x;
+  z[1] = a5[0].y;
+  z[2] = a5[1].x;
+  z[3] = a5[1].y;
 }
 
-// The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16):
-// layers 1-3 on the tensor cores, layers 4-5 on the CUDA cores.  64 TMEM
-// columns: layer 1 -> [0,64); layer 2 -> [0,32) once layer 1's epilogue has
-// read its columns (the epilogue ends with a fence and a barrier before the
-// next issue); layer 3 -> [32,48).  Returns false (uniformly) if an MMA wait
-// timed out.
+// The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16,
+// written by store_input_row): layers 1-3 on the tensor cores, layers 4-5 on
+// the CUDA cores.  64 TMEM columns: layer 1 -> [0,64); layer 2 -> [0,32) once
+// layer 1's epilogue has read its columns (the epilogue ends with a fence and
+// a barrier before the next issue); layer 3 -> [32,48).  Returns false
+// (uniformly) if an MMA wait timed out.
+template <bool BF16>
 __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 16, kNetImageB1, 64, 0);
+  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 16, kNetImageB1, 64, 0);
   wait_layer(c);
-  hidden_epilogue<64>(c, 0, 0, c.bufX);
-  if (threadIdx.x == 0) issue_layer(c, c.bufX, 64, kNetImageB2, 32, 0);
+  hidden_epilogue<64, BF16>(c, 0, c.bufX);
+  // layer 2 reads the input tile for its bias step before its epilogue
+  // overwrites bufY
+  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufX, 64, kNetImageB2, 32, 0, kNetImageB2b);
   wait_layer(c);
-  hidden_epilogue<32>(c, 0, 64, c.bufY);
-  if (threadIdx.x == 0) issue_layer(c, c.bufY, 32, kNetImageB3, 16, 32);
+  hidden_epilogue<32, BF16>(c, 0, c.bufY);
+  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 32, kNetImageB3, 16, 32);
   wait_layer(c);
   tail_layers(c, 32, z);
   // every thread's timeout record is visible after this barrier
