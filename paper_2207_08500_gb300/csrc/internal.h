@@ -55,24 +55,25 @@ struct ClassifyParamsF64 {
   NetF64 net;
 };
 
-// Tensor-core image of the classifier (mixed precision): layers 1-3 as 16-bit
+// Tensor-core image of the classifier (mixed precision): layers 1-4 as 16-bit
 // B operands W_l[out][in] in the K-major canonical layout (K of layer 1
-// padded 6 -> 16).  The biases of layers 1 and 2 ride on the tensor cores:
-// the layer-1 input row carries 1 in columns kOnesCol..kOnesCol+2, B1 holds
-// b1 split into three 16-bit terms (hi + mid + lo, ~24 significant bits) in
-// those columns, and a fifth K-step of layer 2 multiplies the same input tile
-// by the 32 x 16 tile B2b that holds b2's three terms in those columns (zero
-// elsewhere).  Then the FP32 biases of layers 3-5 (b3 at 0, b4 at 16, b5 at
-// 24) and the FP32 weights of layers 4 and 5, stored transposed
-// (W4^T[16][8], W5^T[8][4]) for packed two-output FMAs on the CUDA cores.
+// padded 6 -> 16, N of layer 4 padded 8 -> 16 with zero rows).  The biases of
+// layers 1 and 2 ride on the tensor cores: the layer-1 input row carries 1 in
+// columns kOnesCol..kOnesCol+2, B1 holds b1 split into three 16-bit terms
+// (hi + mid + lo, ~24 significant bits) in those columns, and a fifth K-step
+// of layer 2 multiplies the same input tile by the 32 x 16 tile B2b that
+// holds b2's three terms in those columns (zero elsewhere).  Then the FP32
+// biases of layers 3-5 (b3 at 0, b4 at 16, b5 at 24) and the FP32 weights of
+// layer 5, stored transposed (W5^T[8][4]) for packed two-output FMAs on the
+// CUDA cores.
 constexpr int kOnesCol = 6;
 constexpr int kNetImageB1 = 0;                           // 64 x 16
 constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;   // 32 x 64
 constexpr int kNetImageB2b = kNetImageB2 + 32 * 64 * 2;  // 32 x 16
 constexpr int kNetImageB3 = kNetImageB2b + 32 * 16 * 2;  // 16 x 32
-constexpr int kNetImageBias = kNetImageB3 + 16 * 32 * 2;
-constexpr int kNetImageW4 = kNetImageBias + 32 * 4;
-constexpr int kNetImageW5 = kNetImageW4 + 8 * 16 * 4;
+constexpr int kNetImageB4 = kNetImageB3 + 16 * 32 * 2;   // 16 x 16
+constexpr int kNetImageBias = kNetImageB4 + 16 * 16 * 2;
+constexpr int kNetImageW5 = kNetImageBias + 32 * 4;
 constexpr int kNetImageBytes = kNetImageW5 + 4 * 8 * 4;
 static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");
 

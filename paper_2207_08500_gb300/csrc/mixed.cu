@@ -11,8 +11,9 @@
 // row of the FP32 accumulator from TMEM, applies ReLU, rounds to bf16/fp16
 // (one packed cvt per pair) and stores it as its row of the next layer's
 // input.  The biases of layers 1 and 2 are accumulated by the tensor cores
-// (constant-one input columns, see kOnesCol); layer 3's bias and layers 4-5
-// (16 -> 8 -> 4) run in FP32 on the CUDA cores.  64 TMEM columns per CTA.
+// (constant-one input columns, see kOnesCol); the biases of layers 3-4 are
+// added in FP32 in the epilogues, and layer 5 (8 -> 4) runs in FP32 on the
+// CUDA cores.  64 TMEM columns per CTA.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -147,10 +148,9 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
     }
   };
   const int widths[6] = {6, 64, 32, 16, 8, 4};
-  const int boff[3] = {kNetImageB1, kNetImageB2, kNetImageB3};
-  const int Kpad[3] = {16, 64, 32};
+  const int boff[4] = {kNetImageB1, kNetImageB2, kNetImageB3, kNetImageB4};
+  const int Kpad[4] = {16, 64, 32, 16};
   float* bias = reinterpret_cast<float*>(img + kNetImageBias);
-  float* w4t = reinterpret_cast<float*>(img + kNetImageW4);
   float* w5t = reinterpret_cast<float*>(img + kNetImageW5);
   size_t p = 0;
   for (int l = 0; l < 5; ++l) {
@@ -158,8 +158,7 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
     for (int o = 0; o < nout; ++o)
       for (int i = 0; i < nin; ++i) {
         const double w = net.p[p + (size_t)o * nin + i];
-        if (l < 3) put_bits(boff[l], Kpad[l], o, i, bits(w));
-        else if (l == 3) w4t[i * 8 + o] = (float)w;
+        if (l < 4) put_bits(boff[l], Kpad[l], o, i, bits(w));
         else w5t[i * 4 + o] = (float)w;
       }
     p += (size_t)nout * nin;

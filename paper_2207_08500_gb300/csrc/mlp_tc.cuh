@@ -132,37 +132,41 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, uint8_
   __syncthreads();
 }
 
-// Layer 3's accumulator row (TMEM column col) + bias -> ReLU, then layers
-// 4-5 (16 -> 8 -> 4) in FP32 on the CUDA cores, two outputs per packed FMA
-// (each output still accumulates over its inputs in order, one rounding per
-// FMA).
-__device__ __forceinline__ void tail_layers(const MlpCtx& c, int col, float z[4]) {
-  const uint32_t lane = (uint32_t)(threadIdx.x & ~31) << 16;
+// Layer 3's accumulator row (TMEM columns col3..) + b3 -> ReLU -> 16-bit ->
+// this row of layer 4's operand (K = 16, in bufX, whose layer-2 operand the
+// finished layer-2 MMAs no longer read); layer 4 on the tensor cores (N = 16,
+// rows 8-15 of B4 zero) into TMEM columns col4..; its row + b4 -> ReLU, then
+// layer 5 (8 -> 4) in FP32 on the CUDA cores, two outputs per packed FMA (each
+// output accumulates over its inputs in order, one rounding per FMA).
+template <bool BF16>
+__device__ __forceinline__ void tail_layers(MlpCtx& c, int col3, int col4, float z[4]) {
+  const int t = threadIdx.x;
+  const uint32_t lane = (uint32_t)(t & ~31) << 16;
+  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
   uint32_t r[16];
-  tmem_ld16(c.tmem + lane + (uint32_t)col, r);
+  tmem_ld16(c.tmem + lane + (uint32_t)col3, r);
+  tmem_ld_wait();
+  uint32_t p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 b = reinterpret_cast<const float2*>(bias)[i];
+    const float2 h = __fadd2_rn(make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])), b);
+    p[i] = relu_pack2<BF16>(h.x, h.y);
+  }
+  st_row8(c.bufX, t, 0, 16, p[0], p[1], p[2], p[3]);
+  st_row8(c.bufX, t, 8, 16, p[4], p[5], p[6], p[7]);
+  tc_fence_before();
+  fence_async_smem();
+  __syncthreads();
+  if (t == 0) issue_layer<BF16>(c, c.bufX, 16, kNetImageB4, 16, col4);
+  wait_layer(c);
+  tmem_ld16(c.tmem + lane + (uint32_t)col4, r);
   tmem_ld_wait();
   tc_fence_before();
-  const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
-  const float2* W4t = reinterpret_cast<const float2*>(c.net + kNetImageW4);  // [16][4] pairs
   const float2* W5t = reinterpret_cast<const float2*>(c.net + kNetImageW5);  // [8][2] pairs
-  float h3[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) h3[i] = fmaxf(__uint_as_float(r[i]) + bias[i], 0.0f);
-  float2 a4[4];
-#pragma unroll
-  for (int o = 0; o < 4; ++o) a4[o] = reinterpret_cast<const float2*>(bias + 16)[o];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const float2 h = make_float2(h3[i], h3[i]);
-#pragma unroll
-    for (int o = 0; o < 4; ++o) a4[o] = __ffma2_rn(W4t[i * 4 + o], h, a4[o]);
-  }
   float h4[8];
 #pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    h4[2 * o] = fmaxf(a4[o].x, 0.0f);
-    h4[2 * o + 1] = fmaxf(a4[o].y, 0.0f);
-  }
+  for (int o = 0; o < 8; ++o) h4[o] = fmaxf(__uint_as_float(r[o]) + bias[16 + o], 0.0f);
   float2 a5[2];
 #pragma unroll
   for (int k = 0; k < 2; ++k) a5[k] = reinterpret_cast<const float2*>(bias + 24)[k];
@@ -179,11 +183,11 @@ __device__ __forceinline__ void tail_layers(const MlpCtx& c, int col, float z[4]
 }
 
 // The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16,
-// written by store_input_row): layers 1-3 on the tensor cores, layers 4-5 on
-// the CUDA cores.  64 TMEM columns: layer 1 -> [0,64); layer 2 -> [0,32) once
-// layer 1's epilogue has read its columns (the epilogue ends with a fence and
-// a barrier before the next issue); layer 3 -> [32,48).  Returns false
-// (uniformly) if an MMA wait timed out.
+// written by store_input_row): layers 1-4 on the tensor cores, layer 5 on the
+// CUDA cores.  64 TMEM columns: layer 1 -> [0,64); layer 2 -> [0,32) once
+// layer 1's epilogue has read its columns (each epilogue ends with a fence
+// and a barrier before the next issue); layer 3 -> [32,48); layer 4 ->
+// [48,64).  Returns false (uniformly) if an MMA wait timed out.
 template <bool BF16>
 __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
   if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 16, kNetImageB1, 64, 0);
@@ -196,7 +200,7 @@ __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
   hidden_epilogue<32, BF16>(c, 0, c.bufY);
   if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 32, kNetImageB3, 16, 32);
   wait_layer(c);
-  tail_layers(c, 32, z);
+  tail_layers<BF16>(c, 32, 48, z);
   // every thread's timeout record is visible after this barrier
   return __syncthreads_or(*c.fail) == 0;
 }

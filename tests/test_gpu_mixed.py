@@ -39,18 +39,18 @@ def round16(a, kind):
 
 
 def emulate(net, X, kind):
-    """Layers 1-3 with 16-bit inputs and weights (tensor cores), layers 4-5
-    in FP32 (CUDA cores), FP32 biases."""
+    """Layers 1-4 with 16-bit inputs and weights (tensor cores), layer 5 in
+    FP32 (CUDA cores), biases at (at least) FP32 precision."""
     x = np.asarray(X, dtype=np.float32)
     m = np.maximum(1.0, np.abs(x).max(axis=1)).astype(np.float32)
     h = round16(x / m[:, None], kind)
     L = len(net.layers)
     for l, (W, b) in enumerate(net.layers):
-        Wr = (round16(W, kind) if l < 3 else W.astype(np.float32)).astype(np.float64)
+        Wr = (round16(W, kind) if l < 4 else W.astype(np.float32)).astype(np.float64)
         acc = (h.astype(np.float64) @ Wr.T).astype(np.float32) + b.astype(np.float32)
         if l < L - 1:
             h = np.maximum(acc, 0.0)
-            if l < 2:
+            if l < 3:
                 h = round16(h, kind)
         else:
             z = acc
