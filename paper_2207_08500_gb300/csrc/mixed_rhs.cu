@@ -82,26 +82,30 @@ __device__ __forceinline__ int wrap_idx(int i, int n, int bc) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// FP64 helpers of the mixed path (results within ~1 ulp; the mixed path
-// does not need correctly rounded divisions): hardware reciprocal / reciprocal
-// square-root approximations refined by two Newton steps.
+// FP64 helpers of the mixed path: hardware reciprocal / reciprocal
+// square-root approximations refined by one Newton step (relative error
+// ~1e-10 or better).  That is ample here: every Roe quantity is rounded to
+// FP32 before use, and an error e|F| in a cell flux enters the FP32
+// deviations F - F_ref at ~1e-10 |F|, far below their own rounding; an error
+// in the reference flux itself cancels (F_ref + R L (F - F_ref) reproduces a
+// constant shift up to the FP32 rounding of R L).
 __device__ __forceinline__ double rcp64(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
+  const double e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
 __device__ __forceinline__ double rsqrt64(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double e = fma(-x, y * y, 1.0);
-    y = fma(0.5 * y, e, y);
-  }
-  return y;
+  const double e = fma(-x, y * y, 1.0);
+  return fma(0.5 * y, e, y);
+}
+// x > 0 (and not NaN) on the integer pipe: the binary64 pattern of a
+// positive number (including +inf) is in (0, 0x7ff0000000000000].
+__device__ __forceinline__ bool positive64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000ll;
 }
 // binary64 -> binary32, round to nearest even, on the integer pipe (values
 // below the FP32 normal range flush to zero; no overflow in this use).
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const double q = NDIM == 2 ? fma(v, v, u * u) : u * u;
       const double p = gm1 * (E - 0.5 * rho * q);
       const double Ep = E + p;
-      if (!(rho > 0.0) || !(p > 0.0)) atomicOr(a.status, 1);
+      if (!positive64(rho) || !positive64(p)) atomicOr(a.status, 1);
       cd[CD_S * kMaxCells + tr] = rho * rs;  // sqrt(rho)
       cd[CD_U * kMaxCells + tr] = u;
       cd[CD_V * kMaxCells + tr] = v;
@@ -312,13 +316,15 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const int ca = cb0 + 2 * cstride, cb = cb0 + 3 * cstride;
       const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx);
       const double sa = cd[CD_S * kMaxCells + ca], sb = cd[CD_S * kMaxCells + cb];
-      const double rd = rcp64(sa + sb);
-      const double ut = fma(sb, cd[CD_U * kMaxCells + cb], sa * cd[CD_U * kMaxCells + ca]) * rd;
-      const double vt = fma(sb, cd[CD_V * kMaxCells + cb], sa * cd[CD_V * kMaxCells + ca]) * rd;
-      const double Ht = fma(sb, cd[CD_H * kMaxCells + cb], sa * cd[CD_H * kMaxCells + ca]) * rd;
+      // sqrt(rho)-weighted averages as a + w_b (b - a), w_b = sqrt(rho_b) / (sum)
+      const double wb = sb * rcp64(sa + sb);
+      const double ua = cd[CD_U * kMaxCells + ca], va = cd[CD_V * kMaxCells + ca], Ha = cd[CD_H * kMaxCells + ca];
+      const double ut = fma(wb, cd[CD_U * kMaxCells + cb] - ua, ua);
+      const double vt = fma(wb, cd[CD_V * kMaxCells + cb] - va, va);
+      const double Ht = fma(wb, cd[CD_H * kMaxCells + cb] - Ha, Ha);
       const double qt = fma(vt, vt, ut * ut);
       const double c2 = gm1 * (Ht - 0.5 * qt);
-      if (valid && !(c2 > 0.0)) atomicOr(a.status, 2);
+      if (valid && !positive64(c2)) atomicOr(a.status, 2);
       const double ic = rsqrt64(c2);  // 1/c
       const double ct = c2 * ic;
       const double b1 = gm1 * ic * ic;
