@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
   const int nx = a.nx, ny = a.ny;
   const size_t plane = (size_t)nx * ny;
   const double gm1 = a.gm1;
+  const double hg1 = 0.5 * gm1;
   const float gamma_f = (float)a.gamma;
 
   for (int i = t; i < kNetImageBytes / 16; i += kMlpThreads)
@@ -269,8 +270,8 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const double rr = rs * rs;       // 1/rho
       const double u = U[1] * rr;
       const double v = NDIM == 2 ? U[2] * rr : 0.0;
-      const double q = NDIM == 2 ? fma(v, v, u * u) : u * u;
-      const double p = gm1 * (E - 0.5 * rho * q);
+      const double rq = NDIM == 2 ? fma(U[2], v, U[1] * u) : U[1] * u;  // rho |u|^2
+      const double p = gm1 * fma(-0.5, rq, E);
       const double Ep = E + p;
       if (!positive64(rho) || !positive64(p)) atomicOr(a.status, 1);
       cd[CD_S * kMaxCells + tr] = rho * rs;  // sqrt(rho)
@@ -323,29 +324,36 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const double vt = fma(wb, cd[CD_V * kMaxCells + cb] - va, va);
       const double Ht = fma(wb, cd[CD_H * kMaxCells + cb] - Ha, Ha);
       const double qt = fma(vt, vt, ut * ut);
-      const double c2 = gm1 * (Ht - 0.5 * qt);
+      const double hq = 0.5 * qt;
+      const double c2 = gm1 * (Ht - hq);
       if (valid && !positive64(c2)) atomicOr(a.status, 2);
       const double ic = rsqrt64(c2);  // 1/c
       const double ct = c2 * ic;
-      const double b1 = gm1 * ic * ic;
-      const double b2 = 0.5 * b1 * qt;
-      const double nt = dir == 0 ? ut : vt;
-      const double nc = nt * ic, b1u = b1 * ut, b1v = b1 * vt, hb1 = 0.5 * b1;
+      // rows of L = R^-1 in halves: hb1 = b1/2 = (gamma-1)/(2c^2), hb2 = b2/2 =
+      // hb1 |u|^2/2, hic = 1/(2c); entries that are exact multiples of 2 of
+      // these are scaled after rounding to FP32
+      const double hb1 = hg1 * (ic * ic);
+      const double hb2 = hb1 * hq;
+      const double hic = 0.5 * ic;
+      const double hnc = (dir == 0 ? ut : vt) * hic;
+      const double hb1u = hb1 * ut, hb1v = hb1 * vt;
+      const double hbn = dir == 0 ? hb1u : hb1v;
+      const double sn = hbn + hic, dn = hic - hbn;  // (b1 u_n + 1/c)/2, (1/c - b1 u_n)/2
+      const float fb1u = d2f(hb1u), fb1v = d2f(hb1v), fb1 = d2f(hb1);
+      const float l0 = d2f(hb2 + hnc), l4 = d2f(fma(-2.0, hb2, 1.0)), l12 = d2f(hb2 - hnc);
+      const float fsn = d2f(sn), fdn = d2f(dn);
       float* L = sL + k * 16;
       if (NDIM == 1) {
-        L[0] = d2f(0.5 * (b2 + nc)); L[1] = d2f(0.5 * (-b1u - ic)); L[2] = d2f(hb1); L[3] = 0.f;
-        L[4] = d2f(1.0 - b2); L[5] = d2f(b1u); L[6] = d2f(-b1); L[7] = 0.f;
-        L[8] = d2f(0.5 * (b2 - nc)); L[9] = d2f(0.5 * (-b1u + ic)); L[10] = d2f(hb1); L[11] = 0.f;
+        L[0] = l0; L[1] = -fsn; L[2] = fb1; L[3] = 0.f;
+        L[4] = l4; L[5] = 2.0f * fb1u; L[6] = -2.0f * fb1; L[7] = 0.f;
+        L[8] = l12; L[9] = fdn; L[10] = fb1; L[11] = 0.f;
         L[12] = L[13] = L[14] = L[15] = 0.f;
       } else {
-        const double x0 = dir == 0 ? -ic : 0.0, y0 = dir == 0 ? 0.0 : -ic;
-        L[0] = d2f(0.5 * (b2 + nc)); L[1] = d2f(0.5 * (-b1u + x0)); L[2] = d2f(0.5 * (-b1v + y0));
-        L[3] = d2f(hb1);
-        L[4] = d2f(1.0 - b2); L[5] = d2f(b1u); L[6] = d2f(b1v); L[7] = d2f(-b1);
-        L[8] = d2f(dir == 0 ? -vt : -ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
+        L[0] = l0; L[1] = dir == 0 ? -fsn : -fb1u; L[2] = dir == 0 ? -fb1v : -fsn; L[3] = fb1;
+        L[4] = l4; L[5] = 2.0f * fb1u; L[6] = 2.0f * fb1v; L[7] = -2.0f * fb1;
+        L[8] = -d2f(dir == 0 ? vt : ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
         L[11] = 0.f;
-        L[12] = d2f(0.5 * (b2 - nc)); L[13] = d2f(0.5 * (-b1u - x0)); L[14] = d2f(0.5 * (-b1v - y0));
-        L[15] = d2f(hb1);
+        L[12] = l12; L[13] = dir == 0 ? fdn : -fb1u; L[14] = dir == 0 ? -fb1v : fdn; L[15] = fb1;
       }
       float* R = sRf + k * 5;
       R[0] = d2f(ut); R[1] = d2f(vt); R[2] = d2f(Ht); R[3] = d2f(ct); R[4] = d2f(qt);
