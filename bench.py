@@ -421,7 +421,7 @@ def main():
     ap.add_argument("--vjp-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=48)
-    ap.add_argument("--cpu-crop", type=int, default=96)
+    ap.add_argument("--cpu-crop", type=int, default=384)
     args = ap.parse_args()
     if args.n is None:
         args.n = 2048 if args.precision == "fp64" else 4096
