@@ -63,7 +63,8 @@ constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16
 constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 floats
 constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
 constexpr int kOffBar = kOffRef + 8 * 8 + 8 * 4;  // mbarrier, TMEM address, timeout flag
-constexpr int kFacesSmem = align_up(kOffBar + 16);
+constexpr int kOffWtab = align_up(kOffBar + 16);    // 16 masks x 4 renormalised weights
+constexpr int kFacesSmem = align_up(kOffWtab + 16 * 4 * 4);
 // the guard band's per-warp scratch (4 x 128 floats) reuses the layer-2
 // operand buffer, which is free once a batch's MMAs are done.
 // Five CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
@@ -211,6 +212,10 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
 
   for (int i = t; i < kNetImageBytes / 16; i += kMlpThreads)
     reinterpret_cast<uint4*>(s_net)[i] = reinterpret_cast<const uint4*>(a.net_image)[i];
+  // weight table in shared memory: lanes index it by their own mask, which a
+  // constant-bank read would serialise
+  float4* s_wtab = reinterpret_cast<float4*>(smem + kOffWtab);
+  if (t < 16) s_wtab[t] = make_float4(a.wtab[t][0], a.wtab[t][1], a.wtab[t][2], a.wtab[t][3]);
   if (t == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -445,10 +450,9 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         f[1] = fmaf(a.cand[1][2], ds[4], fmaf(a.cand[1][1], ds[3], a.cand[1][0] * ds[2]));
         f[2] = fmaf(a.cand[2][2], ds[2], fmaf(a.cand[2][1], ds[1], a.cand[2][0] * ds[0]));
         f[3] = fmaf(a.cand[3][3], ds[5], fmaf(a.cand[3][2], ds[4], fmaf(a.cand[3][1], ds[3], a.cand[3][0] * ds[2])));
-        gsum = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (!((eta >> q) & 1u)) gsum = fmaf(a.wtab[eta][q], f[q], gsum);
+        // discarded stencils have weight 0 in the table (fma(0, f, g) = g)
+        const float4 w = s_wtab[eta];
+        gsum = fmaf(w.w, f[3], fmaf(w.z, f[2], fmaf(w.y, f[1], w.x * f[0])));
       }
       const float gh = gsum + __shfl_xor_sync(0xffffffffu, gsum, 1);
       const unsigned eta_other = __shfl_xor_sync(0xffffffffu, eta, 1);
@@ -462,24 +466,25 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         const float ut = Rd[0], vt = Rd[1], Ht = Rd[2], ct = Rd[3], qt = Rd[4];
         const float nt = dir == 0 ? ut : vt;
         const float ntc = nt * ct;
-        float R0, R1, R2, R3 = 0.0f;
+        // row n of R against the waves (u_n - c, entropy, [shear,] u_n + c)
+        // is (A - B, C, [D,] A + B), selected without branches:
+        //   density (1, 0, 1, 0); energy (H, u_n c, |u|^2/2, u_t);
+        //   normal momentum (u_n, c, u_n, 0); tangential (u_t, 0, u_t, 1)
         const int n = m;
-        if (NDIM == 1) {
-          if (n == 0) { R0 = 1.0f; R1 = 1.0f; R2 = 1.0f; }
-          else if (n == 1) { R0 = ut - ct; R1 = ut; R2 = ut + ct; }
-          else { R0 = Ht - ntc; R1 = 0.5f * qt; R2 = Ht + ntc; }
-        } else if (n == 0) { R0 = 1.0f; R1 = 1.0f; R2 = 0.0f; R3 = 1.0f; }
-        else if (n == 3) { R0 = Ht - ntc; R1 = 0.5f * qt; R2 = dir == 0 ? vt : ut; R3 = Ht + ntc; }
-        else if ((n == 1) == (dir == 0)) {  // normal momentum component
-          R0 = nt - ct; R1 = nt; R2 = 0.0f; R3 = nt + ct;
-        } else {                             // tangential momentum component
-          const float tt = dir == 0 ? vt : ut;
-          R0 = tt; R1 = tt; R2 = 1.0f; R3 = tt;
+        const float tt = dir == 0 ? vt : ut;
+        const bool is_rho = n == 0, is_e = n == NV - 1, is_nrm = n == 1 + dir;
+        const float A = is_rho ? 1.0f : (is_e ? Ht : (is_nrm ? nt : tt));
+        const float B = is_e ? ntc : (is_nrm ? ct : 0.0f);
+        const float C = is_rho ? 1.0f : (is_e ? 0.5f * qt : (is_nrm ? nt : tt));
+        float corr = (A - B) * ghq[0];
+        corr = fmaf(C, ghq[1], corr);
+        if (NDIM == 2) {
+          const float D = is_e ? tt : ((is_rho || is_nrm) ? 0.0f : 1.0f);
+          corr = fmaf(D, ghq[2], corr);
+          corr = fmaf(A + B, ghq[3], corr);
+        } else {
+          corr = fmaf(A + B, ghq[2], corr);
         }
-        float corr = R0 * ghq[0];
-        corr = fmaf(R1, ghq[1], corr);
-        corr = fmaf(R2, ghq[2], corr);
-        if (NDIM == 2) corr = fmaf(R3, ghq[3], corr);
         const double Fh = refd[4 + n] + f2d(corr);
         size_t idx;
         if (dir == 0) {
