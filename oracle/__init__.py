@@ -75,6 +75,7 @@ def _load():
         lib.oracle_rhs_cells.argtypes = [P, dp, ctypes.c_int64, i64p, dp]
         lib.oracle_face_masks.argtypes = [P, dp, ctypes.c_int64, i32p, i32p, i32p, u8]
         lib.oracle_rhs_jvp.argtypes = [P, dp, dp, u8, dp, dp]
+        lib.oracle_rhs_jvp_cells.argtypes = [P, dp, dp, u8, ctypes.c_int64, i64p, dp]
         lib.oracle_classify.argtypes = [P, dp, ctypes.c_int64, u8, dp]
         lib.oracle_reconstruct.argtypes = [P, dp, u8]
         lib.oracle_reconstruct.restype = ctypes.c_double
@@ -199,6 +200,19 @@ class Oracle:
                            _ptr(V, ctypes.c_double), _ptr(mask, ctypes.c_uint8),
                            _ptr(f, ctypes.c_double), _ptr(jv, ctypes.c_double))
         return f, jv
+
+    def jvp_cells(self, U, V, mask, cells):
+        """(J V) at the listed cells (flat indices) only: [ncells][nv]."""
+        lib = _load()
+        U = _f64(U).reshape(self.shape())
+        V = _f64(V).reshape(self.shape())
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.empty((cells.size, self.nv), dtype=np.float64)
+        lib.oracle_rhs_jvp_cells(ctypes.byref(self._p), _ptr(U, ctypes.c_double),
+                                 _ptr(V, ctypes.c_double), _ptr(mask, ctypes.c_uint8),
+                                 cells.size, _ptr(cells, ctypes.c_int64), _ptr(out, ctypes.c_double))
+        return out
 
     def classify(self, X):
         lib = _load()

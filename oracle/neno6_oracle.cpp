@@ -573,6 +573,50 @@ int oracle_rhs_jvp(const OracleParams* P, const double* U, const double* V,
   return bad;
 }
 
+// J v of the right-hand side at a list of cells only (flat indices j*nx+i),
+// mask frozen to mask_in, alpha argmax frozen at the primal state; out is
+// [ncells][nv].  Each cell evaluates its own two (four in 2D) faces with the
+// dual-number code of oracle_rhs_jvp, the stencil cells loaded as (U, V).
+int oracle_rhs_jvp_cells(const OracleParams* P, const double* U, const double* V,
+                         const uint8_t* mask_in, int64_t ncells, const int64_t* cells, double* out) {
+  const int nv = P->ndim == 2 ? 4 : 3;
+  OracleParams Q = *P;
+  Q.mask_mode = MASK_GIVEN;
+  const size_t plane = (size_t)Q.nx * Q.ny;
+  auto face = [&](int dir, int f, int line, Dual Fh[4]) {
+    Cell<Dual> st[6];
+    Dual cu[4];
+    for (int k = 0; k < 6; ++k) {
+      const int i = dir == 0 ? ghost(f - 3 + k, Q.nx, Q.bc_x) : line;
+      const int j = dir == 0 ? line : ghost(f - 3 + k, Q.ny, Q.bc_y);
+      const size_t idx = (size_t)j * Q.nx + i;
+      for (int n = 0; n < nv; ++n) cu[n] = Dual(U[n * plane + idx], V[n * plane + idx]);
+      cell_state(Q, dir, cu, st[k]);
+    }
+    uint8_t eta[4] = {0, 0, 0, 0};
+    for (int m = 0; m < nv; ++m)
+      eta[m] = mask_in[dir == 0 ? mask_x_index(Q, m, line, f) : mask_y_index(Q, m, f, line)];
+    return face_flux(Q, dir, st, eta, Fh);
+  };
+  int bad = 0;
+  for (int64_t c = 0; c < ncells; ++c) {
+    const int i = (int)(cells[c] % Q.nx), j = (int)(cells[c] / Q.nx);
+    Dual Fp[4], Fm[4], Gp[4], Gm[4];
+    if (!face(0, i + 1, j, Fp)) bad = 1;
+    if (!face(0, i, j, Fm)) bad = 1;
+    if (Q.ndim == 2) {
+      if (!face(1, j + 1, i, Gp)) bad = 1;
+      if (!face(1, j, i, Gm)) bad = 1;
+    }
+    for (int n = 0; n < nv; ++n) {
+      Dual r = -((Fp[n] - Fm[n]) / Dual(Q.dx));
+      if (Q.ndim == 2) r = r - (Gp[n] - Gm[n]) / Dual(Q.dy);
+      out[c * nv + n] = r.d;
+    }
+  }
+  return bad;
+}
+
 // Sec. 3.1 classifier alone: X [n][6] raw stencil values -> eta bits (and the
 // four logits when logits != null).
 int oracle_classify(const OracleParams* P, const double* X, int64_t n, uint8_t* eta,

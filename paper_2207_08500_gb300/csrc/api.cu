@@ -32,6 +32,7 @@ struct neno6_handle {
   double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
   uint8_t* d_mask = nullptr;       // classifier mask of the adjoint's forward pass (lazily)
   double* d_vjp_rhs = nullptr;     // dU/dt of that forward pass (lazily)
+  double* d_vjp_contrib = nullptr; // per-face adjoint contributions (lazily)
   float* d_params32 = nullptr;     // FP32 parameters, weights-file order
   void* d_bwd_scratch = nullptr;   // per-CTA partial gradients (lazily)
   unsigned long long* d_guard_count = nullptr;
@@ -329,6 +330,7 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_guard_count);
   cudaFree(h->d_mask);
   cudaFree(h->d_vjp_rhs);
+  cudaFree(h->d_vjp_contrib);
   cudaFree(h->d_params32);
   cudaFree(h->d_bwd_scratch);
   delete h;
@@ -473,10 +475,17 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
     if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp: forward");
     mask = h->d_mask;
   }
+  if (!h->d_vjp_contrib) {
+    cudaError_t e = cudaMalloc(&h->d_vjp_contrib, vjp_scratch_bytes(h->cfg.ndim, h->cfg.nx, h->cfg.ny));
+    if (e != cudaSuccess) {
+      h->d_vjp_contrib = nullptr;
+      return cuda_fail(h, e, "rhs_vjp: contribution buffer");
+    }
+  }
   fill_rhs_args(h, p.a);
   p.a.U = U;
   p.a.mask_in = mask;
-  cudaError_t e = launch_rhs_vjp(h->cfg.ndim, p.a, lambda, grad_U, s);
+  cudaError_t e = launch_rhs_vjp(h->cfg.ndim, p.a, lambda, grad_U, h->d_vjp_contrib, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "rhs_vjp launch");
   return NENO6_OK;
 }

@@ -125,7 +125,10 @@ cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
                                   const uint8_t* net_image, bool bf16, int* status, cudaStream_t s);
 cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s);
-cudaError_t launch_rhs_vjp(int ndim, const RhsArgs& a, const double* lam, double* grad, cudaStream_t s);
+// scratch: vjp_scratch_bytes(ndim, nx, ny) bytes (per-face contributions)
+size_t vjp_scratch_bytes(int ndim, int nx, int ny);
+cudaError_t launch_rhs_vjp(int ndim, const RhsArgs& a, const double* lam, double* grad, double* scratch,
+                           cudaStream_t s);
 int mlp_bwd_blocks(long long n);
 size_t mlp_bwd_scratch_bytes(long long n);
 cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const float* params, float* grad,

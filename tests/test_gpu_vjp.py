@@ -115,3 +115,110 @@ def test_autograd_function(lib, net_file):
     ref = g.rhs_vjp(U.detach(), lam)
     assert torch.equal(U.grad, ref)
     assert torch.equal(out.detach(), g.rhs(U.detach()))
+
+
+def _untied_quadrants(n):
+    """The four-quadrant state with u, v and p also modulated by 1e-2 smooth
+    seeded modes (a sum of an x wave and a y wave, so the modulation varies
+    along both axes almost everywhere): piecewise-constant velocities would
+    give exact ties in the LLF maximum |lambda| over a stencil, where the
+    frozen-argmax derivative is one-sided and central differences average the
+    two sides."""
+    U = synth.quadrants_2d(n, n)
+    rho, u, v = U[0], U[1] / U[0], U[2] / U[0]
+    p = 0.4 * (U[3] - 0.5 * rho * (u * u + v * v))
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    rng = np.random.default_rng(77)
+    mods = []
+    for _ in range(3):
+        kx, ky = rng.integers(3, 10, 2)
+        ph = rng.uniform(0, 2 * np.pi, 2)
+        mods.append(1 + 5e-3 * (np.sin(2 * np.pi * kx * X + ph[0]) + np.sin(2 * np.pi * ky * Y + ph[1])))
+    u, v, p = u * mods[0], v * mods[1], p * mods[2]
+    return np.ascontiguousarray(np.stack([rho, rho * u, rho * v, p / 0.4 + 0.5 * rho * (u * u + v * v)]))
+
+
+def _near_tie_cells(U, delta):
+    """Cells inside the stencil of some face whose LLF maximum over its six
+    cells is within delta of the runner-up, for any field, either direction
+    (periodic grid).  Perturbations kept off these cells cannot change an
+    argmax the adjoint holds frozen."""
+    rho, u, v = U[0], U[1] / U[0], U[2] / U[0]
+    p = 0.4 * (U[3] - 0.5 * rho * (u * u + v * v))
+    c = np.sqrt(1.4 * p / rho)
+    out = np.zeros(rho.shape, dtype=bool)
+    for axis, un in ((1, u), (0, v)):
+        for lam in (un - c, un, un + c):
+            L = np.abs(lam)
+            st = np.sort(np.stack([np.roll(L, 3 - k, axis=axis) for k in range(6)]), axis=0)
+            tie = (st[5] - st[4]) < delta
+            for k in range(6):
+                out |= np.roll(tie, k - 3, axis=axis)
+    return out
+
+
+def test_vjp_full_size_against_oracle_jvp(lib, oracle_mod):
+    """The differentiation workload's state itself (1024^2 four quadrants, the
+    trained network): for 48 sampled (cell, field) unit vectors e, <lambda, J e>
+    from the oracle's forward-mode J e at the 13 cells e can reach equals
+    (J^T lambda)[cell, field] from the GPU.  Exact derivatives on both sides
+    (mask and alpha argmax frozen alike), so ties in the LLF maximum do not
+    matter here."""
+    from oracle.weights import Net
+    n = 1024
+    U = synth.quadrants_2d(n, n)
+    g = lib.Neno6(ndim=2, nx=n, ny=n)
+    Ud = torch.from_numpy(U).cuda()
+    _, mask = g.rhs(Ud, want_mask=True)
+    lam = synth.normal(U.shape, seed=12)
+    grad = g.rhs_vjp(Ud, torch.from_numpy(lam).cuda(), mask=mask).cpu().numpy()
+    o = oracle_mod.Oracle(ndim=2, nx=n, ny=n, net=Net.load(lib.DEFAULT_WEIGHTS))
+    mask_h = mask.cpu().numpy()
+    rng = np.random.default_rng(3)
+    V = np.zeros_like(U)
+    for _ in range(48):
+        s, fld = int(rng.integers(0, n * n)), int(rng.integers(0, 4))
+        i, j = s % n, s // n
+        V[fld, j, i] = 1.0
+        cells = sorted({j * n + (i + d) % n for d in range(-3, 4)} | {((j + d) % n) * n + i for d in range(-3, 4)})
+        jv = o.jvp_cells(U, V, mask_h, np.array(cells))
+        terms = np.array([lam[:, c // n, c % n] * jv[r] for r, c in enumerate(cells)])
+        V[fld, j, i] = 0.0
+        lhs, rhs = terms.sum(), grad[fld, j, i]
+        assert abs(lhs - rhs) <= 1e-10 * np.abs(terms).sum(), (s, fld, lhs, rhs)
+
+
+def test_vjp_central_differences_full_size(lib):
+    """Central differences (step 1e-6) of the frozen-mask FP64 RHS at full
+    size, 1024^2, 64 seeded directions v ~ N(0,1) normalised to unit norm,
+    lambda ~ N(0,1), the trained network.  The four-quadrant state has
+    piecewise-constant velocities, i.e. exact ties in the LLF maximum where
+    the frozen-argmax derivative is one-sided, so velocities and pressure are
+    modulated (1e-2) and the directions vanish on the stencils of the faces
+    whose maximum is within 1e-7 of the runner-up (a step moves any |lambda|
+    by at most ~3e-8).  What remains is the rounding and O(h^2) error of the
+    differences, up to ~2e-6 relative here: the bound is 1e-5."""
+    n = 1024
+    Uh = _untied_quadrants(n)
+    excl = _near_tie_cells(Uh, 1e-7)
+    assert excl.mean() < 0.1, excl.mean()
+    keep = torch.from_numpy(~excl).cuda()
+    g = lib.Neno6(ndim=2, nx=n, ny=n)
+    U = torch.from_numpy(Uh).cuda()
+    _, mask = g.rhs(U, want_mask=True)
+    lam = torch.from_numpy(synth.normal(tuple(U.shape), seed=12)).cuda()
+    grad = g.rhs_vjp(U, lam, mask=mask)
+    h = 1e-6
+    worst = 0.0
+    for s in range(64):
+        v = torch.from_numpy(synth.normal(tuple(U.shape), seed=100 + s)).cuda() * keep
+        v /= v.norm()
+        fp = g.rhs(U + h * v, mask_in=mask)
+        fm = g.rhs(U - h * v, mask_in=mask)
+        fd = float(((fp - fm) * lam).sum()) / (2 * h)
+        an = float((grad * v).sum())
+        worst = max(worst, abs(fd - an) / abs(an))
+    assert g.status() == 0
+    print("full-size central differences: worst relative difference %.2e over 64 directions" % worst)
+    assert worst <= 1e-5, worst

@@ -492,3 +492,18 @@ def test_jvp_matches_central_differences(oracle_mod):
         h = 1e-6
         fd = (o.rhs(U + h * V, mask_in=mask) - o.rhs(U - h * V, mask_in=mask)) / (2 * h)
         assert np.abs(fd - jv).max() < 1e-6 * np.abs(jv).max(), np.abs(fd - jv).max()
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("transmissive", "periodic")])
+def test_jvp_cells_equal_full_jvp(oracle_mod, bc):
+    """J v evaluated at chosen cells only is, bit for bit, the full-grid J v
+    there (same dual-number face code, each cell's own faces)."""
+    nx, ny = 13, 9
+    U = synth.smooth_2d(nx, ny, seed=4)
+    o = oracle_mod.Oracle(ndim=2, nx=nx, ny=ny, bc=bc, net=balanced_net(9))
+    _, mask = o.rhs(U, want_mask=True)
+    V = synth.normal(U.shape, seed=61)
+    _, jv = o.jvp(U, V, mask)
+    cells = np.array([0, 5, nx - 1, nx, 4 * nx + 6, nx * ny - 1, nx * (ny - 1)])
+    got = o.jvp_cells(U, V, mask, cells)
+    assert np.array_equal(got, jv.reshape(4, -1)[:, cells].T)
