@@ -206,6 +206,20 @@ int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64
  */
 int neno6_status(neno6_handle* h, int* device_status, void* stream);
 
+/*
+ * neno6_guard_count — synchronise `stream` and return in *count the number
+ * of classifier rows (face, field, side) that the mixed-precision forms
+ * re-evaluated in FP32 on the CUDA cores because some logit fell within
+ * guard_tau of 0 (the 16-bit tensor-core result was not trusted to decide
+ * the sign, Sec. 3.1's 1/2 threshold), summed over the interior faces of every
+ * neno6_rhs / neno6_step evaluation since the handle was created or last
+ * reset; reset != 0 clears the counter afterwards.  One RHS evaluates
+ * 2 * neno6_mask_bytes(h) rows.  FP64 handles report 0.  Not in the paper: an
+ * accuracy diagnostic of the mixed-precision forms.
+ * Errors: ARG, CUDA.
+ */
+int neno6_guard_count(neno6_handle* h, uint64_t* count, int reset, void* stream);
+
 /* neno6_last_error — message of the last failed call on this handle (never
  * NULL; "" when none).  With h == NULL: the last create failure. */
 const char* neno6_last_error(const neno6_handle* h);

@@ -28,7 +28,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.1}
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
-           "neno6_rhs_vjp", "neno6_mlp_bwd")
+           "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count")
 
 
 class Neno6Error(RuntimeError):
@@ -70,6 +70,7 @@ def load_library(path=LIB_PATH):
     lib.neno6_last_error.restype = ctypes.c_char_p
     lib.neno6_rhs_vjp.argtypes = [vp, dp, dp, u8p, dp, vp]
     lib.neno6_mlp_bwd.argtypes = [vp, dp, u8p, i64, vp, vp, vp]
+    lib.neno6_guard_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
     _lib = lib
@@ -211,6 +212,15 @@ class Neno6:
         self._check(self._lib.neno6_mlp_bwd(self._h, _ptr(X), _ptr(labels), X.shape[0], _ptr(grad),
                                             _ptr(loss), _stream()))
         return grad, loss
+
+    def guard_count(self, reset=False):
+        """Synchronise the current stream and return how many classifier rows
+        the mixed-precision path re-evaluated in FP32 (guard band) since the
+        last reset."""
+        v = ctypes.c_uint64(0)
+        self._check(self._lib.neno6_guard_count(self._h, ctypes.byref(v), int(bool(reset)),
+                                                _stream()))
+        return int(v.value)
 
     def status(self):
         """Synchronise the current stream and return (and clear) the device

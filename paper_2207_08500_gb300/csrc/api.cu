@@ -522,6 +522,20 @@ int neno6_status(neno6_handle* h, int* device_status, void* stream) {
   return NENO6_OK;
 }
 
+int neno6_guard_count(neno6_handle* h, uint64_t* count, int reset, void* stream) {
+  if (!h || !count) return NENO6_ERR_ARG;
+  *count = 0;
+  if (!h->d_guard_count) return NENO6_OK;  // FP64 handle: no guard band
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, h->d_guard_count, sizeof v, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->d_guard_count, 0, sizeof v, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "guard count");
+  *count = (uint64_t)v;
+  return NENO6_OK;
+}
+
 const char* neno6_last_error(const neno6_handle* h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }

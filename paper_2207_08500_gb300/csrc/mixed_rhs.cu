@@ -412,7 +412,10 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         s[j] = cref + ds[j];
         mx = fmaxf(mx, fabsf(s[j]));
       }
-      const float inv = 1.0f / mx;
+      // mx >= 1: the approximate reciprocal (within 1 ulp) is ample for an
+      // input that is rounded to 16 bits next
+      float inv;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(mx));
       float x[6];
 #pragma unroll
       for (int j = 0; j < 6; ++j) x[j] = s[j] * inv;
