@@ -15,13 +15,14 @@
 //         on the CUDA cores.
 //
 // Face kernel: persistent CTAs of one warpgroup (five per SM, each with 64
-// TMEM columns).  A block is 64 faces — 64 consecutive x faces of one
-// row, or 4 columns x 16 consecutive y faces.  Per block: stage the stencil
-// cells (ghost cells by wrap / clamp), compute the 64 Roe states once (one
-// thread per face, FP64), then four 128-row tensor-core batches of 16 faces x
-// 4 fields x 2 sides.
+// TMEM columns).  A block is 64 faces on 4 grid lines: 4 rows x 16
+// consecutive x faces, or 4 columns x 16 consecutive y faces.  Per block:
+// stage the 4 x 21 stencil cells (ghost cells by wrap / clamp), compute the
+// 64 Roe states once (one thread per face, FP64) while the other half of the
+// CTA forms the LLF alpha of every (face, field), then four 128-row
+// tensor-core batches of 16 faces x 4 fields x 2 sides.
 //
-// Reference shift.  The block's first stencil cell is a reference state
+// Reference shift.  A cell near the block's centre is a reference state
 // (U_ref, F_ref); every cell is staged as the FP64 difference (U - U_ref,
 // F - F_ref) rounded to FP32.  The reconstruction is linear and reproduces
 // constants, and the alpha terms of the two sides cancel, so
@@ -43,11 +44,18 @@ namespace {
 using namespace tc;
 using namespace tcmlp;
 
-constexpr int kFaces = 64;       // faces per block
-constexpr int kYCols = 4;        // y block: 4 columns x 16 faces
-constexpr int kYFaces = kFaces / kYCols;
-constexpr int kMaxCells = kYCols * (kYFaces + 5);  // 84 (x block: 69)
-static_assert(kMaxCells <= 128 && kFaces + 5 <= 128, "one stencil cell per thread");
+constexpr int kFaces = 64;                     // faces per block
+constexpr int kLines = 4;                      // grid lines per block
+constexpr int kLineFaces = kFaces / kLines;    // consecutive faces per line
+constexpr int kLineCells = kLineFaces + 5;     // stencil cells per line
+constexpr int kMaxCells = kLines * kLineCells;  // 84
+static_assert(kMaxCells <= 128, "one stencil cell per thread");
+// Staged cell c of an x block is (line c / kLineCells, position c % kLineCells);
+// of a y block (position c / kLines, line c % kLines).  The reference cell
+// sits near the block's centre (line 1, position 10), which keeps the FP32
+// deviations small: at most 10 cells along and 2 across the lines.
+constexpr int kRefX = 1 * kLineCells + kLineCells / 2;
+constexpr int kRefY = (kLineCells / 2) * kLines + 1;
 constexpr int kAlign = 128;
 
 constexpr int align_up(int x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -59,8 +67,12 @@ constexpr int kOffCellD = align_up(kOffBufY + kBufYBytes);      // 4 x kMaxCells
 // per cell 8 floats (U_n, F_n deviations interleaved), then per cell 2 floats
 // (normal velocity, sound speed)
 constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8);
-constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);   // kFaces x 16 floats
-constexpr int kOffR = align_up(kOffL + kFaces * 16 * 4);          // kFaces x 5 floats
+// rows of L/2 for the fields (u_n - c, entropy, u_n + c): kFaces x 12 floats
+// (the shear row of 2D is rebuilt from the Roe velocity); LLF alpha per
+// field: kFaces x 4 floats
+constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);
+constexpr int kOffA = align_up(kOffL + kFaces * 12 * 4);
+constexpr int kOffR = align_up(kOffA + kFaces * 4 * 4);           // kFaces x 5 floats
 constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
 constexpr int kOffBar = kOffRef + 8 * 8 + 8 * 4;  // mbarrier, TMEM address, timeout flag
 constexpr int kOffWtab = align_up(kOffBar + 16);    // 16 masks x 4 renormalised weights
@@ -190,6 +202,52 @@ __device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* w
   }
 }
 
+// Geometry of block `blk`: the x blocks come first (kLines rows x kLineFaces
+// faces), then the y blocks (kLines columns x kLineFaces faces).
+struct BlockGeom {
+  int dir;      // 0: x faces, 1: y faces
+  int row, f0;  // x block: first row, first face of each line
+  int i0, g0;   // y block: first column, first face of each line
+};
+__device__ __forceinline__ BlockGeom block_geom(long long blk, const FacesMixedArgs& a) {
+  BlockGeom b{0, 0, 0, 0, 0};
+  if (blk < a.nblk_x) {
+    b.row = (int)(blk / a.bxf) * kLines;
+    b.f0 = (int)(blk % a.bxf) * kLineFaces;
+  } else {
+    const long long q = blk - a.nblk_x;
+    b.dir = 1;
+    b.i0 = (int)(q % a.byc) * kLines;
+    b.g0 = (int)(q / a.byc) * kLineFaces;
+  }
+  return b;
+}
+// Grid cell (j * nx + i) of staged cell c: ghost cells along the lines by
+// periodic wrap or clamp; lines beyond the grid clamp to its last line (their
+// faces are not written).
+__device__ __forceinline__ size_t staged_cell(const BlockGeom& b, int c, const FacesMixedArgs& a) {
+  int gi, gj;
+  if (b.dir == 0) {
+    gi = wrap_idx(b.f0 - 3 + c % kLineCells, a.nx, a.bcx);
+    gj = min(b.row + c / kLineCells, a.ny - 1);
+  } else {
+    gi = min(b.i0 + c % kLines, a.nx - 1);
+    gj = wrap_idx(b.g0 - 3 + c / kLines, a.ny, a.bcy);
+  }
+  return (size_t)gj * a.nx + gi;
+}
+// Staged index of face k's first stencil cell (the others follow at stride
+// 1 in x blocks, kLines in y blocks).
+__device__ __forceinline__ int face_cb0(int dir, int k) {
+  return dir == 0 ? (k / kLineFaces) * kLineCells + k % kLineFaces : k;
+}
+// Face k of the block exists on the grid (x faces 0..nx of rows 0..ny-1,
+// y faces 0..ny of columns 0..nx-1).
+__device__ __forceinline__ bool face_valid(const BlockGeom& b, int k, int nx, int ny) {
+  return b.dir == 0 ? (b.f0 + k % kLineFaces <= nx && b.row + k / kLineFaces < ny)
+                    : (b.g0 + k / kLines <= ny && b.i0 + k % kLines < nx);
+}
+
 template <int NDIM, bool BF16>
 __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
@@ -199,6 +257,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
   float2* cuc = reinterpret_cast<float2*>(cf + 8 * kMaxCells);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
+  float* sA = reinterpret_cast<float*>(smem + kOffA);
   float* ws = reinterpret_cast<float*>(smem + kOffBufX) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
@@ -238,36 +297,18 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
   float* sRf = reinterpret_cast<float*>(smem + kOffR);           // ut, vt, Ht, ct, qt per face
   for (long long blk = blockIdx.x; blk < nblk && !failed; blk += gridDim.x) {
     // ---- block geometry
-    const int dir = blk < a.nblk_x ? 0 : 1;
-    int row = 0, f0 = 0, i0 = 0, g0 = 0, ncells, cstride;
-    if (dir == 0) {
-      row = (int)(blk / a.bxf);
-      f0 = (int)(blk % a.bxf) * kFaces;
-      ncells = kFaces + 5;
-      cstride = 1;
-    } else {
-      const long long b = blk - a.nblk_x;
-      i0 = (int)(b % a.byc) * kYCols;
-      g0 = (int)(b / a.byc) * kYFaces;
-      ncells = kYCols * (kYFaces + 5);
-      cstride = kYCols;
-    }
+    const BlockGeom bg = block_geom(blk, a);
+    const int dir = bg.dir;
+    const int cstride = dir == 0 ? 1 : kLines;
+    const int ref_c = dir == 0 ? kRefX : kRefY;
     // thread index rotated by one warp per block, so that the partly
     // occupied cell and Roe phases fall on different warps (and SM
     // sub-partitions) from block to block
     const int tr = (t + (int)((blk & 3) * 32)) & (kMlpThreads - 1);
     // ---- stencil cells (one per thread): FP64 Roe inputs and fluxes
     double U[NV], F[4];
-    if (tr < ncells) {
-      int gi, gj;
-      if (dir == 0) {
-        gi = wrap_idx(f0 - 3 + tr, nx, a.bcx);
-        gj = row;
-      } else {
-        gi = min(i0 + (tr % kYCols), nx - 1);
-        gj = wrap_idx(g0 - 3 + tr / kYCols, ny, a.bcy);
-      }
-      const size_t g = (size_t)gj * nx + gi;
+    if (tr < kMaxCells) {
+      const size_t g = staged_cell(bg, tr, a);
 #pragma unroll
       for (int n = 0; n < NV; ++n) U[n] = a.U[n * plane + g];
       const double rho = U[0], E = U[NV - 1];
@@ -291,7 +332,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
       }
       cuc[tr] = make_float2(d2f(dir == 0 ? u : v), sqrtf(gamma_f * d2f(p) * d2f(rr)));
-      if (tr == 0) {  // the block's reference state
+      if (tr == ref_c) {  // the block's reference state
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
           refd[n] = n < NV ? U[n] : 0.0;
@@ -303,7 +344,7 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
     }
     __syncthreads();
     // ---- deviations from the reference, rounded to FP32
-    if (tr < ncells) {
+    if (tr < kMaxCells) {
       float w[8];
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
@@ -314,13 +355,14 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       dst[0] = make_float4(w[0], w[1], w[2], w[3]);
       dst[1] = make_float4(w[4], w[5], w[6], w[7]);
     }
-    // ---- Roe average and eigenvectors (FP64), one thread per face
-    const int tq = (tr + 64) & (kMlpThreads - 1);  // the other half of the CTA
+    // ---- Roe average and eigenvectors (FP64), one thread per face; the
+    // other half of the CTA forms the LLF alpha of every (face, field)
+    const int tq = (tr + 64) & (kMlpThreads - 1);
     if (tq < kFaces) {
       const int k = tq;
-      const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
+      const int cb0 = face_cb0(dir, k);
       const int ca = cb0 + 2 * cstride, cb = cb0 + 3 * cstride;
-      const bool valid = dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx);
+      const bool valid = face_valid(bg, k, nx, ny);
       const double sa = cd[CD_S * kMaxCells + ca], sb = cd[CD_S * kMaxCells + cb];
       // sqrt(rho)-weighted averages as a + w_b (b - a), w_b = sqrt(rho_b) / (sum)
       const double wb = sb * rcp64(sa + sb);
@@ -335,8 +377,9 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const double ic = rsqrt64(c2);  // 1/c
       const double ct = c2 * ic;
       // rows of L = R^-1 in halves: hb1 = b1/2 = (gamma-1)/(2c^2), hb2 = b2/2 =
-      // hb1 |u|^2/2, hic = 1/(2c); entries that are exact multiples of 2 of
-      // these are scaled after rounding to FP32
+      // hb1 |u|^2/2, hic = 1/(2c).  L/2 is stored (the split's factor 1/2,
+      // exact in binary): its entries are these halves rounded to FP32 and
+      // scaled by exact powers of 2.
       const double hb1 = hg1 * (ic * ic);
       const double hb2 = hb1 * hq;
       const double hic = 0.5 * ic;
@@ -347,21 +390,34 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const float fb1u = d2f(hb1u), fb1v = d2f(hb1v), fb1 = d2f(hb1);
       const float l0 = d2f(hb2 + hnc), l4 = d2f(fma(-2.0, hb2, 1.0)), l12 = d2f(hb2 - hnc);
       const float fsn = d2f(sn), fdn = d2f(dn);
-      float* L = sL + k * 16;
+      // three stored rows: the u_n - c, entropy and u_n + c fields
+      float4* L = reinterpret_cast<float4*>(sL + k * 12);
+      const float h = 0.5f;
       if (NDIM == 1) {
-        L[0] = l0; L[1] = -fsn; L[2] = fb1; L[3] = 0.f;
-        L[4] = l4; L[5] = 2.0f * fb1u; L[6] = -2.0f * fb1; L[7] = 0.f;
-        L[8] = l12; L[9] = fdn; L[10] = fb1; L[11] = 0.f;
-        L[12] = L[13] = L[14] = L[15] = 0.f;
+        L[0] = make_float4(h * l0, -h * fsn, h * fb1, 0.f);
+        L[1] = make_float4(h * l4, fb1u, -fb1, 0.f);
+        L[2] = make_float4(h * l12, h * fdn, h * fb1, 0.f);
       } else {
-        L[0] = l0; L[1] = dir == 0 ? -fsn : -fb1u; L[2] = dir == 0 ? -fb1v : -fsn; L[3] = fb1;
-        L[4] = l4; L[5] = 2.0f * fb1u; L[6] = 2.0f * fb1v; L[7] = -2.0f * fb1;
-        L[8] = -d2f(dir == 0 ? vt : ut); L[9] = dir == 0 ? 0.f : 1.f; L[10] = dir == 0 ? 1.f : 0.f;
-        L[11] = 0.f;
-        L[12] = l12; L[13] = dir == 0 ? fdn : -fb1u; L[14] = dir == 0 ? -fb1v : fdn; L[15] = fb1;
+        L[0] = make_float4(h * l0, dir == 0 ? -h * fsn : -h * fb1u, dir == 0 ? -h * fb1v : -h * fsn, h * fb1);
+        L[1] = make_float4(h * l4, fb1u, fb1v, -fb1);
+        L[2] = make_float4(h * l12, dir == 0 ? h * fdn : -h * fb1u, dir == 0 ? -h * fb1v : h * fdn, h * fb1);
       }
       float* R = sRf + k * 5;
       R[0] = d2f(ut); R[1] = d2f(vt); R[2] = d2f(Ht); R[3] = d2f(ct); R[4] = d2f(qt);
+    } else {
+      // LLF alpha per field: max over the six stencil cells of |u_n - c|,
+      // |u_n| and |u_n + c|
+      const int k = tq - kFaces;
+      const int cb0 = face_cb0(dir, k);
+      float am = 0.0f, a0 = 0.0f, ap = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const float2 uc = cuc[cb0 + j * cstride];
+        am = fmaxf(am, fabsf(uc.x - uc.y));
+        a0 = fmaxf(a0, fabsf(uc.x));
+        ap = fmaxf(ap, fabsf(uc.x + uc.y));
+      }
+      reinterpret_cast<float4*>(sA)[k] = NDIM == 2 ? make_float4(am, a0, a0, ap) : make_float4(am, a0, ap, 0.0f);
     }
     __syncthreads();
     // ---- four tensor-core batches of 16 faces x 4 fields x 2 sides
@@ -370,18 +426,18 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       const int fld = (t >> 1) & 3;
       const int m = min(fld, NV - 1);
       const int side = t & 1;
-      const int cb0 = dir == 0 ? k : (k / kYCols) * kYCols + (k % kYCols);
-      const bool valid = fld < NV &&
-                         (dir == 0 ? (f0 + k <= nx) : (g0 + k / kYCols <= ny && i0 + k % kYCols < nx));
-      const float4 Lv = *reinterpret_cast<const float4*>(sL + k * 16 + m * 4);
-      const float Lr[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
-      float alpha = 0.0f;
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const float2 uc = cuc[cb0 + j * cstride];
-        const float lam = m == 0 ? uc.x - uc.y : (m == NV - 1 ? uc.x + uc.y : uc.x);
-        alpha = fmaxf(alpha, fabsf(lam));
+      const int cb0 = face_cb0(dir, k);
+      const bool valid = fld < NV && face_valid(bg, k, nx, ny);
+      // row m of L/2; the shear row of 2D is (-u_t, e_t) / 2
+      float4 Lv;
+      if (NDIM == 2 && m == 2) {
+        const float tt = sRf[k * 5 + (dir == 0 ? 1 : 0)];
+        Lv = make_float4(-0.5f * tt, dir == 0 ? 0.0f : 0.5f, dir == 0 ? 0.5f : 0.0f, 0.0f);
+      } else {
+        Lv = reinterpret_cast<const float4*>(sL + k * 12)[m == 0 ? 0 : (m == NV - 1 ? 2 : 1)];
       }
+      const float Lr[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
+      const float alpha = sA[k * 4 + m];
       const float sgn_alpha = side ? -alpha : alpha;
       // reference part of this side's split flux: (L F_ref +- alpha L U_ref)/2
       float vr = Lr[0] * reff[0], gr = Lr[0] * reff[4];
@@ -390,18 +446,18 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         vr = fmaf(Lr[n], reff[n], vr);
         gr = fmaf(Lr[n], reff[4 + n], gr);
       }
-      const float cref = 0.5f * fmaf(sgn_alpha, vr, gr);
+      const float cref = fmaf(sgn_alpha, vr, gr);
       float ds[6];  // deviations of the split flux from the reference part
 #pragma unroll
       for (int j = 0; j < 6; ++j) {
-        // (v, g) = L_m . (U_j, F_j) deviations, both in one packed FMA chain
+        // (v, g) = L_m/2 . (U_j, F_j) deviations, both in one packed FMA chain
         const float4* src = reinterpret_cast<const float4*>(cf + 8 * (cb0 + j * cstride));
         const float4 p0 = src[0], p1 = src[1];
         float2 vg = __fmul2_rn(make_float2(Lr[0], Lr[0]), make_float2(p0.x, p0.y));
         vg = __ffma2_rn(make_float2(Lr[1], Lr[1]), make_float2(p0.z, p0.w), vg);
         vg = __ffma2_rn(make_float2(Lr[2], Lr[2]), make_float2(p1.x, p1.y), vg);
         if (NV == 4) vg = __ffma2_rn(make_float2(Lr[3], Lr[3]), make_float2(p1.z, p1.w), vg);
-        const float val = 0.5f * fmaf(sgn_alpha, vg.x, vg.y);
+        const float val = fmaf(sgn_alpha, vg.x, vg.y);
         // "+" side: stencil i-2..i+3; "-" side: its mirror image
         if (side == 0) ds[j] = val;
         else ds[5 - j] = val;
@@ -491,11 +547,11 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         const double Fh = refd[4 + n] + f2d(corr);
         size_t idx;
         if (dir == 0) {
-          const int f = f0 + k;
-          idx = ((size_t)n * ny + row) * (nx + 1) + f;
+          const int f = bg.f0 + k % kLineFaces, r = bg.row + k / kLineFaces;
+          idx = ((size_t)n * ny + r) * (nx + 1) + f;
           a.Fx[idx] = Fh;
         } else {
-          const int g = g0 + k / kYCols, i = i0 + k % kYCols;
+          const int g = bg.g0 + k / kLines, i = bg.i0 + k % kLines;
           idx = ((size_t)n * (ny + 1) + g) * nx + i;
           a.Fy[idx] = Fh;
           idx += (size_t)NV * ny * (nx + 1);
@@ -573,10 +629,12 @@ void build_guard_image(const NetF64& net, float* g) {
 }
 
 cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
-  a.bxf = (a.nx + 1 + kFaces - 1) / kFaces;
-  a.nblk_x = (long long)a.bxf * a.ny;
-  a.byc = (a.nx + kYCols - 1) / kYCols;
-  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kYFaces - 1) / kYFaces) : 0;
+  // x blocks: nx + 1 faces per row in runs of kLineFaces, rows in groups of
+  // kLines; y blocks: columns in groups of kLines, ny + 1 faces per column
+  a.bxf = (a.nx + 1 + kLineFaces - 1) / kLineFaces;
+  a.nblk_x = (long long)a.bxf * ((a.ny + kLines - 1) / kLines);
+  a.byc = (a.nx + kLines - 1) / kLines;
+  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kLineFaces - 1) / kLineFaces) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
   // persistent grid: five resident CTAs per SM (registers, shared memory,
   // 64 TMEM columns each)
