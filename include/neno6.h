@@ -51,6 +51,8 @@ extern "C" {
 /* device status bits (neno6_status) */
 #define NENO6_STATUS_NONPHYSICAL_CELL 1 /* rho <= 0 or p <= 0 (or NaN)   */
 #define NENO6_STATUS_NONPHYSICAL_ROE 2  /* Roe-averaged c^2 <= 0         */
+#define NENO6_STATUS_TIMEOUT 4          /* a tensor-core wait gave up    */
+#define NENO6_STATUS_BAD_SAMPLE 8       /* mlp_train: index out of range */
 
 /* neno6_config.precision */
 #define NENO6_FP64 0        /* everything in binary64 (bit-exact masks)    */
@@ -197,6 +199,31 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
  */
 int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, float* grad,
                   float* loss, void* stream);
+
+/*
+ * neno6_mlp_train — retrain the classifier on the GPU: mini-batch Adam on the
+ * mean binary cross entropy of Eq. (Crossentropy) as Sec. 3.3 and Table 2
+ * prescribe (Adam of Kingma & Ba with beta1 = 0.9, beta2 = 0.999, epsilon =
+ * 1e-8; the caller supplies batch 175, the per-epoch learning rate of the
+ * schedule and a fresh permutation each epoch).  Runs ceil(n_perm / batch)
+ * steps in order: step s takes the samples perm[s*batch ..], normalises them
+ * as in Eq. (normalizainput), and updates every parameter once.  FP32
+ * arithmetic, deterministic.  The handle's own network is not used or changed.
+ *   X        [n][6] float64 stencil values;  labels [n] uint8 (bit k = eta_k).
+ *   perm     [n_perm] int32 sample indices (device); an index outside [0, n)
+ *            skips that sample and sets NENO6_STATUS_BAD_SAMPLE.
+ *   batch    1 <= batch <= 192 (the last batch may be shorter).
+ *   params   [3228] float32 in/out, weights-file order.
+ *   adam_m, adam_v  [3228] float32 in/out Adam moments (zero to start).
+ *   adam_t0  Adam steps already taken with these moments (bias correction).
+ *   lr       learning rate of these steps.
+ *   loss_sum nullable float64 scalar out: the sum over the steps of each
+ *            batch's mean loss (before its update).
+ * Errors: ARG, SHAPE, ALIGN, CUDA.
+ */
+int neno6_mlp_train(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, const int32_t* perm,
+                    int64_t n_perm, int batch, float* params, float* adam_m, float* adam_v, int64_t adam_t0,
+                    double lr, double* loss_sum, void* stream);
 
 /*
  * neno6_status — synchronise `stream`, return the latched device status bits

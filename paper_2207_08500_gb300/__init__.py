@@ -28,7 +28,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.1}
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
-           "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count")
+           "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train")
 
 
 class Neno6Error(RuntimeError):
@@ -70,6 +70,8 @@ def load_library(path=LIB_PATH):
     lib.neno6_last_error.restype = ctypes.c_char_p
     lib.neno6_rhs_vjp.argtypes = [vp, dp, dp, u8p, dp, vp]
     lib.neno6_mlp_bwd.argtypes = [vp, dp, u8p, i64, vp, vp, vp]
+    lib.neno6_mlp_train.argtypes = [vp, dp, u8p, i64, vp, i64, ctypes.c_int, vp, vp, vp, i64,
+                                    ctypes.c_double, vp, vp]
     lib.neno6_guard_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
@@ -212,6 +214,25 @@ class Neno6:
         self._check(self._lib.neno6_mlp_bwd(self._h, _ptr(X), _ptr(labels), X.shape[0], _ptr(grad),
                                             _ptr(loss), _stream()))
         return grad, loss
+
+    def mlp_train(self, X, labels, perm, params, adam_m, adam_v, adam_t0, lr, batch=175):
+        """Mini-batch Adam steps on the classifier loss (neno6_mlp_train):
+        batches of `batch` samples in the order of perm (int32 CUDA tensor of
+        sample indices).  params / adam_m / adam_v: float32 CUDA tensors
+        [3228], updated in place.  Returns the float64 CUDA scalar holding the
+        sum over the steps of each batch's mean loss."""
+        assert X.is_cuda and X.dtype == torch.float64 and X.shape[-1] == 6
+        assert labels.is_cuda and labels.dtype == torch.uint8 and labels.numel() == X.shape[0]
+        assert perm.is_cuda and perm.dtype == torch.int32
+        for t in (params, adam_m, adam_v):
+            assert t.is_cuda and t.dtype == torch.float32 and t.numel() == 3228 and t.is_contiguous()
+        X, labels, perm = X.contiguous(), labels.contiguous(), perm.contiguous()
+        loss_sum = torch.zeros(1, dtype=torch.float64, device=X.device)
+        self._check(self._lib.neno6_mlp_train(self._h, _ptr(X), _ptr(labels), X.shape[0], _ptr(perm),
+                                              perm.numel(), int(batch), _ptr(params), _ptr(adam_m),
+                                              _ptr(adam_v), int(adam_t0), float(lr), _ptr(loss_sum),
+                                              _stream()))
+        return loss_sum
 
     def guard_count(self, reset=False):
         """Synchronise the current stream and return how many classifier rows

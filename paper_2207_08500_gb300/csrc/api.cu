@@ -509,6 +509,37 @@ int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64
   return NENO6_OK;
 }
 
+int neno6_mlp_train(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, const int32_t* perm,
+                    int64_t n_perm, int batch, float* params, float* adam_m, float* adam_v, int64_t adam_t0,
+                    double lr, double* loss_sum, void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (n < 1 || n >= (1ll << 31) || n_perm < 1 || n_perm >= (1ll << 31))
+    return fail(h, NENO6_ERR_SHAPE, "mlp_train: need 1 <= n, n_perm < 2^31");
+  if (batch < 1 || batch > kMaxTrainBatch) return fail(h, NENO6_ERR_SHAPE, "mlp_train: need 1 <= batch <= 192");
+  if (!X || !labels || !perm || !params || !adam_m || !adam_v) return fail(h, NENO6_ERR_ARG, "mlp_train: null pointer");
+  if (adam_t0 < 0 || !(lr >= 0.0)) return fail(h, NENO6_ERR_ARG, "mlp_train: need adam_t0 >= 0, lr >= 0");
+  if (!aligned(X, 8) || !aligned(perm, 4) || !aligned(params, 4) || !aligned(adam_m, 4) || !aligned(adam_v, 4) ||
+      (loss_sum && !aligned(loss_sum, 8)))
+    return fail(h, NENO6_ERR_ALIGN, "mlp_train: misaligned");
+  MlpTrainArgs a;
+  a.X = X;
+  a.y = labels;
+  a.n = n;
+  a.perm = perm;
+  a.n_perm = n_perm;
+  a.batch = batch;
+  a.params = params;
+  a.m = adam_m;
+  a.v = adam_v;
+  a.t0 = adam_t0;
+  a.lr = (float)lr;
+  a.loss_sum = loss_sum;
+  a.status = h->d_status;
+  cudaError_t e = launch_mlp_train(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mlp_train launch");
+  return NENO6_OK;
+}
+
 int neno6_status(neno6_handle* h, int* device_status, void* stream) {
   if (!h || !device_status) return NENO6_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;

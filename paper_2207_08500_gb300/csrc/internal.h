@@ -133,6 +133,24 @@ int mlp_bwd_blocks(long long n);
 size_t mlp_bwd_scratch_bytes(long long n);
 cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const float* params, float* grad,
                            float* loss, void* scratch, cudaStream_t s);
+// On-GPU classifier training: mini-batch Adam over a permutation of samples.
+constexpr int kMaxTrainBatch = 192;
+struct MlpTrainArgs {
+  const double* X;     // [n][6] raw stencils
+  const uint8_t* y;    // [n] label bits
+  long long n;
+  const int32_t* perm;  // [n_perm] sample indices, batches in this order
+  long long n_perm;
+  int batch;           // 1..kMaxTrainBatch; the last batch may be shorter
+  float* params;       // [kNetParams] in/out
+  float* m;            // [kNetParams] Adam first moments, in/out
+  float* v;            // [kNetParams] Adam second moments, in/out
+  long long t0;        // Adam steps taken before this call
+  float lr;
+  double* loss_sum;    // nullable: sum over the steps of the batch-mean loss
+  int* status;
+};
+cudaError_t launch_mlp_train(const MlpTrainArgs& a, cudaStream_t s);
 cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
                               unsigned long long* smax, int* status, cudaStream_t s);
 

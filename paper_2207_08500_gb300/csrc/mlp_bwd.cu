@@ -11,26 +11,17 @@
 // thread accumulates ~25 of the 3228 parameter gradients over the tile's
 // samples.  Per-CTA partial sums are reduced in a fixed order by a second
 // kernel, so the result is deterministic.
-#include <cmath>
-
 #include "internal.h"
+#include "mlp_fb.cuh"
 
 namespace neno6 {
 namespace {
 
+using namespace mlpfb;
+
 constexpr int kT = 128;        // samples per tile = threads per CTA
 constexpr int kPitch = kT + 1;  // feature-major rows, padded against bank conflicts
-// parameter offsets (per layer W[out][in] then b[out])
-__host__ __device__ constexpr int wofs(int l) { return l == 0 ? 0 : l == 1 ? 448 : l == 2 ? 2528 : l == 3 ? 3056 : 3192; }
-__host__ __device__ constexpr int wid(int l) { return l == 0 ? 6 : l == 1 ? 64 : l == 2 ? 32 : l == 3 ? 16 : l == 4 ? 8 : 4; }
-// staged rows: inputs x0 (6) x1 (64) x2 (32) x3 (16) x4 (8); deltas d1..d5
-constexpr int kX0 = 0, kX1 = 6, kX2 = 70, kX3 = 102, kX4 = 118;
-constexpr int kD1 = 126, kD2 = 190, kD3 = 222, kD4 = 238, kD5 = 246, kRows = 250;
 constexpr int kSmemFloats = kNetParams + kRows * kPitch;
-
-__device__ __forceinline__ float softplus(float z) {  // log(1 + e^z), stable
-  return fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
-}
 
 __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ X, const uint8_t* __restrict__ y,
                                                      long long n, const float* __restrict__ params,
@@ -51,129 +42,17 @@ __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long s = tile * kT + t;
     const bool live = s < n;
-    // ---- forward (Eq. (normalizainput), (reconstuction), (activationfunction))
-    float x0[6], m = 1.0f;
+    float xr[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      x0[j] = live ? (float)X[s * 6 + j] : 0.0f;
-      m = fmaxf(m, fabsf(x0[j]));
-    }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      x0[j] = x0[j] / m;
-      st[(kX0 + j) * kPitch + t] = x0[j];
-    }
-    float h1[64];
-#pragma unroll
-    for (int o = 0; o < 64; ++o) {
-      float a = W[wofs(0) + 384 + o];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) a = fmaf(W[wofs(0) + o * 6 + i], x0[i], a);
-      h1[o] = fmaxf(a, 0.0f);
-      st[(kX1 + o) * kPitch + t] = h1[o];
-    }
-    float h2[32];
-#pragma unroll
-    for (int o = 0; o < 32; ++o) {
-      float a = W[wofs(1) + 2048 + o];
-#pragma unroll
-      for (int i = 0; i < 64; ++i) a = fmaf(W[wofs(1) + o * 64 + i], h1[i], a);
-      h2[o] = fmaxf(a, 0.0f);
-      st[(kX2 + o) * kPitch + t] = h2[o];
-    }
-    float h3[16];
-#pragma unroll
-    for (int o = 0; o < 16; ++o) {
-      float a = W[wofs(2) + 512 + o];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) a = fmaf(W[wofs(2) + o * 32 + i], h2[i], a);
-      h3[o] = fmaxf(a, 0.0f);
-      st[(kX3 + o) * kPitch + t] = h3[o];
-    }
-    float h4[8];
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      float a = W[wofs(3) + 128 + o];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) a = fmaf(W[wofs(3) + o * 16 + i], h3[i], a);
-      h4[o] = fmaxf(a, 0.0f);
-      st[(kX4 + o) * kPitch + t] = h4[o];
-    }
-    // ---- output: loss and dL/dz = (sigma(z) - y) / (n S); ReLU masks of the
-    // backward pass are re-read from the staged activations (fewer live
-    // registers)
-    asm volatile("" ::: "memory");
-    float d5[4];
-    const unsigned lab = live ? y[s] : 0u;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float z = W[wofs(4) + 32 + k];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) z = fmaf(W[wofs(4) + k * 8 + i], h4[i], z);
-      const float yk = (float)((lab >> k) & 1u);
-      const float sig = 1.0f / (1.0f + __expf(-z));
-      // -[y log s + (1-y) log(1-s)] = softplus(z) - y z
-      if (live) loss += (double)(softplus(z) - yk * z);
-      d5[k] = live ? (sig - yk) * inv_nS : 0.0f;
-      st[(kD5 + k) * kPitch + t] = d5[k];
-    }
-    // ---- backward: delta_l = (W_{l+1}^T delta_{l+1}) * relu'(pre-activation)
-    float d4[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float a = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) a = fmaf(W[wofs(4) + k * 8 + i], d5[k], a);
-      d4[i] = st[(kX4 + i) * kPitch + t] > 0.0f ? a : 0.0f;
-      st[(kD4 + i) * kPitch + t] = d4[i];
-    }
-    float d3[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      float a = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) a = fmaf(W[wofs(3) + k * 16 + i], d4[k], a);
-      d3[i] = st[(kX3 + i) * kPitch + t] > 0.0f ? a : 0.0f;
-      st[(kD3 + i) * kPitch + t] = d3[i];
-    }
-    float d2[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      float a = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) a = fmaf(W[wofs(2) + k * 32 + i], d3[k], a);
-      d2[i] = st[(kX2 + i) * kPitch + t] > 0.0f ? a : 0.0f;
-      st[(kD2 + i) * kPitch + t] = d2[i];
-    }
-#pragma unroll
-    for (int i = 0; i < 64; ++i) {
-      float a = 0.0f;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) a = fmaf(W[wofs(1) + k * 64 + i], d2[k], a);
-      st[(kD1 + i) * kPitch + t] = st[(kX1 + i) * kPitch + t] > 0.0f ? a : 0.0f;
-    }
+    for (int j = 0; j < 6; ++j) xr[j] = live ? (float)X[s * 6 + j] : 0.0f;
+    sample_fwd_bwd<kPitch>(W, st, t, live, xr, live ? y[s] : 0u, inv_nS, loss);
     __syncthreads();
     // ---- parameter gradients over the tile: dW = delta^T x, db = sum delta
 #pragma unroll
     for (int q = 0; q < kPer; ++q) {
       const int p = t + q * kT;
       if (p >= kNetParams) break;
-      int l = 4;
-      while (l > 0 && p < wofs(l)) --l;
-      const int nin = wid(l), nout = wid(l + 1);
-      const int r = p - wofs(l);
-      const int drow = (l == 0 ? kD1 : l == 1 ? kD2 : l == 2 ? kD3 : l == 3 ? kD4 : kD5);
-      const int xrow = (l == 0 ? kX0 : l == 1 ? kX1 : l == 2 ? kX2 : l == 3 ? kX3 : kX4);
-      float a = 0.0f;
-      if (r < nout * nin) {
-        const float* dp = st + (drow + r / nin) * kPitch;
-        const float* xp = st + (xrow + r % nin) * kPitch;
-        for (int j = 0; j < kT; ++j) a = fmaf(dp[j], xp[j], a);
-      } else {
-        const float* dp = st + (drow + (r - nout * nin)) * kPitch;
-        for (int j = 0; j < kT; ++j) a += dp[j];
-      }
-      acc[q] += a;
+      acc[q] += param_grad<kPitch>(st, p, kT);
     }
     __syncthreads();
   }

@@ -1,0 +1,162 @@
+// Per-sample forward and backward pass of the classifier's training loss,
+// shared by the gradient kernel (mlp_bwd.cu) and the training kernel
+// (mlp_train.cu).  The network is the 6-64-32-16-8-4 ReLU MLP of Sec. 3.1,
+// the loss the mean binary cross entropy of Eq. (Crossentropy) over the S = 4
+// sigmoid outputs, all in FP32.
+//
+// One thread per sample.  The weights W (weights-file order: per layer
+// W[out][in] then b[out]) are broadcast from shared memory; every layer's
+// input and every delta are staged feature-major in shared memory, column
+// `col` of rows of length PITCH, for the parameter-gradient sums that follow.
+#pragma once
+
+#include <cmath>
+
+#include "internal.h"
+
+namespace neno6 {
+namespace mlpfb {
+
+// parameter offsets and layer widths
+__host__ __device__ constexpr int wofs(int l) { return l == 0 ? 0 : l == 1 ? 448 : l == 2 ? 2528 : l == 3 ? 3056 : 3192; }
+__host__ __device__ constexpr int wid(int l) { return l == 0 ? 6 : l == 1 ? 64 : l == 2 ? 32 : l == 3 ? 16 : l == 4 ? 8 : 4; }
+// staged rows: inputs x0 (6) x1 (64) x2 (32) x3 (16) x4 (8); deltas d1..d5
+constexpr int kX0 = 0, kX1 = 6, kX2 = 70, kX3 = 102, kX4 = 118;
+constexpr int kD1 = 126, kD2 = 190, kD3 = 222, kD4 = 238, kD5 = 246, kRows = 250;
+
+__device__ __forceinline__ float softplus(float z) {  // log(1 + e^z), stable
+  return fmaxf(z, 0.0f) + log1pf(__expf(-fabsf(z)));
+}
+
+// Forward and backward pass of one sample (raw stencil x, label bits lab;
+// `live` false stages zeros).  inv_nS = 1 / (4 n) for a batch of n samples.
+// Adds the sample's BCE sum over the four outputs to `loss`.
+template <int PITCH>
+__device__ __forceinline__ void sample_fwd_bwd(const float* W, float* st, int col, bool live, const float (&xr)[6],
+                                               unsigned lab, float inv_nS, double& loss) {
+  // ---- forward (Eq. (normalizainput), (reconstuction), (activationfunction))
+  float x0[6], m = 1.0f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    x0[j] = live ? xr[j] : 0.0f;
+    m = fmaxf(m, fabsf(x0[j]));
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    x0[j] = x0[j] / m;
+    st[(kX0 + j) * PITCH + col] = x0[j];
+  }
+  float h1[64];
+#pragma unroll
+  for (int o = 0; o < 64; ++o) {
+    float a = W[wofs(0) + 384 + o];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) a = fmaf(W[wofs(0) + o * 6 + i], x0[i], a);
+    h1[o] = fmaxf(a, 0.0f);
+    st[(kX1 + o) * PITCH + col] = h1[o];
+  }
+  float h2[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) {
+    float a = W[wofs(1) + 2048 + o];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) a = fmaf(W[wofs(1) + o * 64 + i], h1[i], a);
+    h2[o] = fmaxf(a, 0.0f);
+    st[(kX2 + o) * PITCH + col] = h2[o];
+  }
+  float h3[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) {
+    float a = W[wofs(2) + 512 + o];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) a = fmaf(W[wofs(2) + o * 32 + i], h2[i], a);
+    h3[o] = fmaxf(a, 0.0f);
+    st[(kX3 + o) * PITCH + col] = h3[o];
+  }
+  float h4[8];
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float a = W[wofs(3) + 128 + o];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a = fmaf(W[wofs(3) + o * 16 + i], h3[i], a);
+    h4[o] = fmaxf(a, 0.0f);
+    st[(kX4 + o) * PITCH + col] = h4[o];
+  }
+  // ---- output: loss and dL/dz = (sigma(z) - y) / (n S); ReLU masks of the
+  // backward pass are re-read from the staged activations (fewer live
+  // registers)
+  asm volatile("" ::: "memory");
+  float d5[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float z = W[wofs(4) + 32 + k];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z = fmaf(W[wofs(4) + k * 8 + i], h4[i], z);
+    const float yk = (float)((lab >> k) & 1u);
+    const float sig = 1.0f / (1.0f + __expf(-z));
+    // -[y log s + (1-y) log(1-s)] = softplus(z) - y z
+    if (live) loss += (double)(softplus(z) - yk * z);
+    d5[k] = live ? (sig - yk) * inv_nS : 0.0f;
+    st[(kD5 + k) * PITCH + col] = d5[k];
+  }
+  // ---- backward: delta_l = (W_{l+1}^T delta_{l+1}) * relu'(pre-activation)
+  float d4[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a = fmaf(W[wofs(4) + k * 8 + i], d5[k], a);
+    d4[i] = st[(kX4 + i) * PITCH + col] > 0.0f ? a : 0.0f;
+    st[(kD4 + i) * PITCH + col] = d4[i];
+  }
+  float d3[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a = fmaf(W[wofs(3) + k * 16 + i], d4[k], a);
+    d3[i] = st[(kX3 + i) * PITCH + col] > 0.0f ? a : 0.0f;
+    st[(kD3 + i) * PITCH + col] = d3[i];
+  }
+  float d2[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a = fmaf(W[wofs(2) + k * 32 + i], d3[k], a);
+    d2[i] = st[(kX2 + i) * PITCH + col] > 0.0f ? a : 0.0f;
+    st[(kD2 + i) * PITCH + col] = d2[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 64; ++i) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) a = fmaf(W[wofs(1) + k * 64 + i], d2[k], a);
+    st[(kD1 + i) * PITCH + col] = st[(kX1 + i) * PITCH + col] > 0.0f ? a : 0.0f;
+  }
+}
+
+// Gradient of parameter p summed over the first `ns` staged samples:
+// dW = sum delta x (the layer's input), db = sum delta.
+template <int PITCH>
+__device__ __forceinline__ float param_grad(const float* st, int p, int ns) {
+  int l = 4;
+  while (l > 0 && p < wofs(l)) --l;
+  const int nin = wid(l), nout = wid(l + 1);
+  const int r = p - wofs(l);
+  const int drow = (l == 0 ? kD1 : l == 1 ? kD2 : l == 2 ? kD3 : l == 3 ? kD4 : kD5);
+  const int xrow = (l == 0 ? kX0 : l == 1 ? kX1 : l == 2 ? kX2 : l == 3 ? kX3 : kX4);
+  float a = 0.0f;
+  if (r < nout * nin) {
+    const float* dp = st + (drow + r / nin) * PITCH;
+    const float* xp = st + (xrow + r % nin) * PITCH;
+    for (int j = 0; j < ns; ++j) a = fmaf(dp[j], xp[j], a);
+  } else {
+    const float* dp = st + (drow + (r - nout * nin)) * PITCH;
+    for (int j = 0; j < ns; ++j) a += dp[j];
+  }
+  return a;
+}
+
+}  // namespace mlpfb
+}  // namespace neno6
