@@ -304,11 +304,7 @@ def run_ours(args, rank, world):
         g64.close()
         del Uv, lam, gv, maskv, Xs, ys
 
-    # max over ranks
-    vals = torch.tensor([ms, e2e_ms, rhs_avg], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    ms, e2e_ms, rhs_avg = vals.tolist()
+    ms, e2e_ms, rhs_avg = max_over_ranks([ms, e2e_ms, rhs_avg], world, dev)
 
     cells = n * n
     value = cells * args.steps * world / (ms * 1e-3) / 1e6
@@ -353,6 +349,16 @@ def run_ours(args, rank, world):
         "weights_sha256": weights_sha256(weights),
     }
     return line
+
+
+def max_over_ranks(values, world, device):
+    """Element-wise maximum of `values` (floats) over all ranks of the
+    default process group (the job's time is its slowest rank's)."""
+    import torch
+    vals = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+    return vals.tolist()
 
 
 def oracle_free_init(seed):
