@@ -332,6 +332,17 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         F[0] = U[2]; F[1] = U[1] * v; F[2] = fma(U[2], v, p); F[3] = Ep * v;
       }
       cuc[tr] = make_float2(d2f(dir == 0 ? u : v), sqrtf(gamma_f * d2f(p) * d2f(rr)));
+      if (tr >= kFaces) {
+        // cells kFaces.. are staged by Roe-phase threads: their deviations
+        // are formed by the alpha-phase threads, from the layer-2 operand
+        // buffer (free between blocks)
+        double* sc = reinterpret_cast<double*>(smem + kOffBufX) + (tr - kFaces) * 8;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          sc[n] = n < NV ? U[n] : 0.0;
+          sc[4 + n] = F[n];
+        }
+      }
       if (tr == ref_c) {  // the block's reference state
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
@@ -343,17 +354,26 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
       }
     }
     __syncthreads();
-    // ---- deviations from the reference, rounded to FP32
-    if (tr < kMaxCells) {
+    // ---- deviations from the reference, rounded to FP32 (the mass flux is a
+    // momentum component: its deviation is that component's)
+    auto deviations = [&](int c, const double* Uc, const double* Fc) {
       float w[8];
 #pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        w[2 * n] = n < NV ? d2f(U[n] - refd[n]) : 0.0f;
-        w[2 * n + 1] = d2f(F[n] - refd[4 + n]);
-      }
-      float4* dst = reinterpret_cast<float4*>(cf + 8 * tr);
+      for (int n = 0; n < 4; ++n) w[2 * n] = n < NV ? d2f(Uc[n] - refd[n]) : 0.0f;
+      w[1] = NDIM == 2 && dir == 1 ? w[4] : w[2];
+#pragma unroll
+      for (int n = 1; n < 4; ++n) w[2 * n + 1] = d2f(Fc[n] - refd[4 + n]);
+      float4* dst = reinterpret_cast<float4*>(cf + 8 * c);
       dst[0] = make_float4(w[0], w[1], w[2], w[3]);
       dst[1] = make_float4(w[4], w[5], w[6], w[7]);
+    };
+    if (tr < kFaces) {
+      double Uo[4] = {U[0], U[1], NV > 2 ? U[2] : 0.0, NV > 3 ? U[NV - 1] : 0.0};
+      deviations(tr, Uo, F);
+      if (tr < kMaxCells - kFaces) {
+        const double* sc = reinterpret_cast<const double*>(smem + kOffBufX) + tr * 8;
+        deviations(kFaces + tr, sc, sc + 4);
+      }
     }
     // ---- Roe average and eigenvectors (FP64), one thread per face; the
     // other half of the CTA forms the LLF alpha of every (face, field)
@@ -447,20 +467,31 @@ __global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __gri
         gr = fmaf(Lr[n], reff[4 + n], gr);
       }
       const float cref = fmaf(sgn_alpha, vr, gr);
-      float ds[6];  // deviations of the split flux from the reference part
+      // deviations of the split flux from the reference part, in this side's
+      // stencil order ("+" side cells i-2..i+3, "-" side the mirror image
+      // i+3..i-2).  Both sides of a (face, field), adjacent lanes, project the
+      // same six cells: each lane projects the first three cells of its own
+      // order and takes the other three, (v, g) pairs, from its partner.
+      float ds[6];
+      float2 vg[3];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
+      for (int q = 0; q < 3; ++q) {
         // (v, g) = L_m/2 . (U_j, F_j) deviations, both in one packed FMA chain
+        const int j = side ? 5 - q : q;
         const float4* src = reinterpret_cast<const float4*>(cf + 8 * (cb0 + j * cstride));
         const float4 p0 = src[0], p1 = src[1];
-        float2 vg = __fmul2_rn(make_float2(Lr[0], Lr[0]), make_float2(p0.x, p0.y));
-        vg = __ffma2_rn(make_float2(Lr[1], Lr[1]), make_float2(p0.z, p0.w), vg);
-        vg = __ffma2_rn(make_float2(Lr[2], Lr[2]), make_float2(p1.x, p1.y), vg);
-        if (NV == 4) vg = __ffma2_rn(make_float2(Lr[3], Lr[3]), make_float2(p1.z, p1.w), vg);
-        const float val = fmaf(sgn_alpha, vg.x, vg.y);
-        // "+" side: stencil i-2..i+3; "-" side: its mirror image
-        if (side == 0) ds[j] = val;
-        else ds[5 - j] = val;
+        vg[q] = __fmul2_rn(make_float2(Lr[0], Lr[0]), make_float2(p0.x, p0.y));
+        vg[q] = __ffma2_rn(make_float2(Lr[1], Lr[1]), make_float2(p0.z, p0.w), vg[q]);
+        vg[q] = __ffma2_rn(make_float2(Lr[2], Lr[2]), make_float2(p1.x, p1.y), vg[q]);
+        if (NV == 4) vg[q] = __ffma2_rn(make_float2(Lr[3], Lr[3]), make_float2(p1.z, p1.w), vg[q]);
+        ds[q] = fmaf(sgn_alpha, vg[q].x, vg[q].y);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        // the partner's q-th cell is this side's (5 - q)-th
+        const float v = __shfl_xor_sync(0xffffffffu, vg[q].x, 1);
+        const float g = __shfl_xor_sync(0xffffffffu, vg[q].y, 1);
+        ds[5 - q] = fmaf(sgn_alpha, v, g);
       }
       float mx = 1.0f, s[6];
 #pragma unroll
