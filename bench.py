@@ -335,7 +335,9 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": kname, "flops_counted": fl_note,
                      "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": round(traffic_bytes(prec, n)),
+                     "traffic_source": TRAFFIC_NOTE[prec == "fp64"],
                      "peak_source": "FP64 pipe: 2 DFMA per clock per SM (ncu's sustained peak) "
                                     "x 152 SMs x 2 flops x 2070 MHz",
                      "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3)},
@@ -349,6 +351,21 @@ def run_ours(args, rank, world):
         "weights_sha256": weights_sha256(weights),
     }
     return line
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the current kernels at 2048^2 (profiles/*.md), scaled by cells
+# for other grids (the traffic is U once, the face fluxes once and the halo
+# re-reads, all proportional to the cells)
+TRAFFIC_2048 = {True: 141.2e6 + 96.6e6, False: 271.4e6 + 233.7e6}
+TRAFFIC_NOTE = {True: "rhs_fp64_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
+                      "capture at 2048^2, scaled by cells",
+                False: "faces_mixed_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
+                       "capture at 2048^2, scaled by cells"}
+
+
+def traffic_bytes(prec, n):
+    return TRAFFIC_2048[prec == "fp64"] * (n * n) / 2048.0 ** 2
 
 
 def max_over_ranks(values, world, device):
