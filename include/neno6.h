@@ -200,6 +200,37 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
 int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, float* grad,
                   float* loss, void* stream);
 
+/* scalar laws (neno6_scalar_rhs / neno6_scalar_solve) */
+#define NENO6_LAW_ADVECTION 0 /* f(u) = u       (Sec. 4.1) */
+#define NENO6_LAW_BURGERS 1   /* f(u) = u^2 / 2 (Sec. 4.2) */
+
+/*
+ * neno6_scalar_rhs — du/dt of a scalar conservation law u_t + f(u)_x = 0 on
+ * the handle's 1D grid with the same reconstruction as the Euler path (Sec.
+ * 4.1-4.2, Algorithm 2): local Lax-Friedrichs split with alpha = max over the
+ * six stencil cells of |f'(u)|, the "-" side mirrored about the face, the
+ * handle's classifier / mask mode / linear weights, the conservative
+ * difference of Eq. (approximateEq).  FP64, bit-identical to the oracle.
+ *   law       NENO6_LAW_ADVECTION or NENO6_LAW_BURGERS.
+ *   u, dudt   [nx] float64 (device).
+ *   mask_out  nullable [nx + 1] uint8: face f (between cells f-1 and f) has
+ *             the "+" side's eta bits in bits 0-3, the "-" side's in 4-7.
+ * The handle must be 1D and FP64 (else UNSUPPORTED).
+ * Errors: ARG, ALIGN, UNSUPPORTED, CUDA.
+ */
+int neno6_scalar_rhs(neno6_handle* h, int law, const double* u, double* dudt, uint8_t* mask_out, void* stream);
+
+/*
+ * neno6_scalar_solve — advance u (in place) to t_end with SSP-RK3 at the fixed
+ * step dt = cfl * dx / max_i |f'(u_i)| of the initial data (the scalar cases
+ * of Sec. 4.1-4.2), the last step clipped to end exactly at t_end.
+ * Synchronises `stream` once to read the initial wave speed.
+ *   nsteps_out  nullable: number of steps taken.
+ * Errors: ARG, ALIGN, UNSUPPORTED, CUDA.
+ */
+int neno6_scalar_solve(neno6_handle* h, int law, double* u, double cfl, double t_end, int64_t* nsteps_out,
+                       void* stream);
+
 /*
  * neno6_mlp_train — retrain the classifier on the GPU: mini-batch Adam on the
  * mean binary cross entropy of Eq. (Crossentropy) as Sec. 3.3 and Table 2

@@ -22,13 +22,15 @@ PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}
 BC = {"periodic": 0, "transmissive": 1}
 LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
 MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
+LAW = {"advection": 0, "burgers": 1}
 # logit band re-evaluated in FP32 by the mixed-precision path
 DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.1}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
-           "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train")
+           "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train",
+           "neno6_scalar_rhs", "neno6_scalar_solve")
 
 
 class Neno6Error(RuntimeError):
@@ -72,6 +74,9 @@ def load_library(path=LIB_PATH):
     lib.neno6_mlp_bwd.argtypes = [vp, dp, u8p, i64, vp, vp, vp]
     lib.neno6_mlp_train.argtypes = [vp, dp, u8p, i64, vp, i64, ctypes.c_int, vp, vp, vp, i64,
                                     ctypes.c_double, vp, vp]
+    lib.neno6_scalar_rhs.argtypes = [vp, ctypes.c_int, dp, dp, u8p, vp]
+    lib.neno6_scalar_solve.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_int64), vp]
     lib.neno6_guard_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
@@ -214,6 +219,31 @@ class Neno6:
         self._check(self._lib.neno6_mlp_bwd(self._h, _ptr(X), _ptr(labels), X.shape[0], _ptr(grad),
                                             _ptr(loss), _stream()))
         return grad, loss
+
+    def _scalar(self, u, name="u"):
+        if not (u.is_cuda and u.dtype == torch.float64 and u.is_contiguous() and u.numel() == self.nx
+                and u.dim() == 1):
+            raise ValueError("%s must be a contiguous float64 CUDA vector of length %d" % (name, self.nx))
+        return u
+
+    def scalar_rhs(self, law, u, want_mask=False, out=None):
+        """du/dt of the scalar law `law` ("advection" or "burgers") on this
+        1D FP64 grid (neno6_scalar_rhs); optionally the face masks [nx+1]."""
+        u = self._scalar(u)
+        out = torch.empty_like(u) if out is None else self._scalar(out, "out")
+        mask = torch.empty(self.nx + 1, dtype=torch.uint8, device=u.device) if want_mask else None
+        self._check(self._lib.neno6_scalar_rhs(self._h, LAW[law], _ptr(u), _ptr(out), _ptr(mask),
+                                               _stream()))
+        return (out, mask) if want_mask else out
+
+    def scalar_solve(self, law, u, cfl, t_end):
+        """Advance u in place to t_end at the fixed step cfl dx / max|f'(u0)|
+        (neno6_scalar_solve); returns the number of steps."""
+        u = self._scalar(u)
+        ns = ctypes.c_int64(0)
+        self._check(self._lib.neno6_scalar_solve(self._h, LAW[law], _ptr(u), float(cfl), float(t_end),
+                                                 ctypes.byref(ns), _stream()))
+        return int(ns.value)
 
     def mlp_train(self, X, labels, perm, params, adam_m, adam_v, adam_t0, lr, batch=175):
         """Mini-batch Adam steps on the classifier loss (neno6_mlp_train):

@@ -32,6 +32,7 @@ SOURCES = {
     "vjp.cu": ["-fmad=false"],
     "mlp_bwd.cu": [],
     "mlp_train.cu": [],
+    "scalar.cu": ["-fmad=false"],
 }
 
 

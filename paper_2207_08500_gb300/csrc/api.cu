@@ -40,6 +40,7 @@ struct neno6_handle {
   size_t state_elems = 0;
   RhsParamsF64 rhs_params;        // launch parameter blocks (copied at launch)
   ClassifyParamsF64 cls_params;
+  ScalarParams scalar_params;
   std::string err;
 };
 
@@ -506,6 +507,97 @@ int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64
   }
   cudaError_t e = launch_mlp_bwd(X, labels, n, h->d_params32, grad, loss, h->d_bwd_scratch, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mlp_bwd launch");
+  return NENO6_OK;
+}
+
+namespace {
+
+int scalar_check(neno6_handle* h, int law, const void* u, const char* who) {
+  if (!h) return NENO6_ERR_ARG;
+  if (h->cfg.ndim != 1 || h->cfg.precision != NENO6_FP64)
+    return fail(h, NENO6_ERR_UNSUPPORTED, std::string(who) + ": needs a 1D FP64 handle");
+  if (law != NENO6_LAW_ADVECTION && law != NENO6_LAW_BURGERS)
+    return fail(h, NENO6_ERR_ARG, std::string(who) + ": unknown law");
+  if (!u) return fail(h, NENO6_ERR_ARG, std::string(who) + ": null pointer");
+  if (!aligned(u, 8)) return fail(h, NENO6_ERR_ALIGN, std::string(who) + ": misaligned");
+  if (h->cfg.mask_mode == kMaskGiven) return fail(h, NENO6_ERR_UNSUPPORTED, std::string(who) + ": mask mode");
+  return NENO6_OK;
+}
+
+// face fluxes of u into h->d_faces (nx + 1 values)
+int scalar_faces(neno6_handle* h, int law, const double* u, uint8_t* mask_out, cudaStream_t s) {
+  int rc = ensure_faces(h);
+  if (rc != NENO6_OK) return rc;
+  ScalarParams& p = h->scalar_params;
+  fill_rhs_args(h, p.a);
+  p.net = h->net;
+  p.law = law;
+  p.u = u;
+  p.F = h->d_faces;
+  p.mask_out = mask_out;
+  cudaError_t e = launch_scalar_faces(p, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "scalar face kernel");
+  return NENO6_OK;
+}
+
+}  // namespace
+
+int neno6_scalar_rhs(neno6_handle* h, int law, const double* u, double* dudt, uint8_t* mask_out, void* stream) {
+  int rc = scalar_check(h, law, u, "scalar_rhs");
+  if (rc != NENO6_OK) return rc;
+  if (!dudt) return fail(h, NENO6_ERR_ARG, "scalar_rhs: null pointer");
+  if (!aligned(dudt, 8)) return fail(h, NENO6_ERR_ALIGN, "scalar_rhs: misaligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = scalar_faces(h, law, u, mask_out, s);
+  if (rc != NENO6_OK) return rc;
+  cudaError_t e = launch_scalar_diff(h->d_faces, u, u, dudt, h->cfg.nx, h->cfg.dx, 0, 0.0, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "scalar difference kernel");
+  return NENO6_OK;
+}
+
+int neno6_scalar_solve(neno6_handle* h, int law, double* u, double cfl, double t_end, int64_t* nsteps_out,
+                       void* stream) {
+  int rc = scalar_check(h, law, u, "scalar_solve");
+  if (rc != NENO6_OK) return rc;
+  if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "scalar_solve: need cfl > 0, t_end >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->cfg.nx;
+  if (!h->d_stage) {
+    cudaError_t e = cudaMalloc(&h->d_stage, 2 * h->state_elems * sizeof(double));
+    if (e != cudaSuccess) {
+      h->d_stage = nullptr;
+      return cuda_fail(h, e, "scalar_solve: stage buffers");
+    }
+  }
+  // initial wave speed -> the fixed step (one synchronisation)
+  cudaError_t e = launch_scalar_speed(u, n, law, h->d_smax, s);
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, h->d_smax, sizeof bits, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "scalar_solve: wave speed");
+  double amax;
+  std::memcpy(&amax, &bits, sizeof amax);
+  if (!(amax > 0.0)) return fail(h, NENO6_ERR_ARG, "scalar_solve: zero wave speed");
+  const double dt = cfl * h->cfg.dx / amax;
+  double* u1 = h->d_stage;
+  double* u2 = h->d_stage + n;
+  double t = 0.0;
+  int64_t steps = 0;
+  const double* in[3] = {u, u1, u2};
+  double* out[3] = {u1, u2, u};
+  while (t < t_end) {
+    double step = dt;
+    if (t + step > t_end) step = t_end - t;
+    for (int st = 1; st <= 3; ++st) {
+      rc = scalar_faces(h, law, in[st - 1], nullptr, s);
+      if (rc != NENO6_OK) return rc;
+      e = launch_scalar_diff(h->d_faces, in[st - 1], u, out[st - 1], n, h->cfg.dx, st, step, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "scalar stage kernel");
+    }
+    t = t + step;
+    ++steps;
+  }
+  if (nsteps_out) *nsteps_out = steps;
   return NENO6_OK;
 }
 

@@ -133,6 +133,20 @@ int mlp_bwd_blocks(long long n);
 size_t mlp_bwd_scratch_bytes(long long n);
 cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const float* params, float* grad,
                            float* loss, void* scratch, cudaStream_t s);
+// Scalar conservation laws (1D): law 0 linear advection, 1 Burgers.
+struct ScalarParams {
+  RhsArgs a;        // grid, boundary, mask mode, candidates, weights
+  NetF64 net;
+  int law;
+  const double* u;  // [nx]
+  double* F;        // [nx + 1] face fluxes
+  uint8_t* mask_out;  // nullable [nx + 1]
+};
+cudaError_t launch_scalar_faces(const ScalarParams& p, cudaStream_t s);
+cudaError_t launch_scalar_diff(const double* F, const double* in, const double* u0, double* out, int n,
+                               double dx, int stage, double h, cudaStream_t s);
+cudaError_t launch_scalar_speed(const double* u, int n, int law, unsigned long long* amax, cudaStream_t s);
+
 // On-GPU classifier training: mini-batch Adam over a permutation of samples.
 constexpr int kMaxTrainBatch = 192;
 struct MlpTrainArgs {
