@@ -322,6 +322,9 @@ def run_ours(args, rank, world):
         launches_per_step = 8
     achieved = fl / (rhs_avg * 1e-3) / 1e12
     peak = fp64_peak_tflops()
+    # the FP64 and FP32 FMA rates measured on this GPU in the same run
+    meas64 = neno6.pipe_peak("fp64") / 1e12
+    meas32 = neno6.pipe_peak("fp32") / 1e12
     state_bytes = U.numel() * 8
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -340,7 +343,10 @@ def run_ours(args, rank, world):
                      "traffic_source": TRAFFIC_NOTE[prec == "fp64"],
                      "peak_source": "FP64 pipe: 2 DFMA per clock per SM (ncu's sustained peak) "
                                     "x 152 SMs x 2 flops x 2070 MHz",
-                     "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3)},
+                     "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3),
+                     "fp64_fma_measured_tflops": round(meas64, 4),
+                     "frac_of_measured_fp64": round(achieved / meas64, 4),
+                     "fp32_fma_measured_tflops": round(meas32, 2)},
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
                 "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
         "gpu_launches": launches_per_step * args.steps,

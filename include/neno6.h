@@ -257,6 +257,16 @@ int neno6_mlp_train(neno6_handle* h, const double* X, const uint8_t* labels, int
                     double lr, double* loss_sum, void* stream);
 
 /*
+ * neno6_pipe_peak — measured fused multiply-add rate of this GPU, a
+ * measurement aid for roofline figures (no counterpart in the paper): eight
+ * independent FMA chains per thread, 8 CTAs of 256 threads per SM, timed with
+ * CUDA events on `stream` (synchronises it).  which = 0: FP64 (DFMA), 1: FP32
+ * (FFMA).  *flops_per_s receives 2 x FMAs / s for the whole GPU.  Needs no
+ * handle.  Errors: ARG, CUDA.
+ */
+int neno6_pipe_peak(int which, double* flops_per_s, void* stream);
+
+/*
  * neno6_status — synchronise `stream`, return the latched device status bits
  * (NENO6_STATUS_*) in *device_status and clear them.  Returns
  * NENO6_ERR_NONPHYSICAL when any bit was set, NENO6_ERR_CUDA when the stream

@@ -30,7 +30,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.1}
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
            "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train",
-           "neno6_scalar_rhs", "neno6_scalar_solve")
+           "neno6_scalar_rhs", "neno6_scalar_solve", "neno6_pipe_peak")
 
 
 class Neno6Error(RuntimeError):
@@ -77,6 +77,7 @@ def load_library(path=LIB_PATH):
     lib.neno6_scalar_rhs.argtypes = [vp, ctypes.c_int, dp, dp, u8p, vp]
     lib.neno6_scalar_solve.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int64), vp]
+    lib.neno6_pipe_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.neno6_guard_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
@@ -281,6 +282,17 @@ class Neno6:
         if rc not in (OK, -6):
             self._check(rc)
         return v.value
+
+
+def pipe_peak(which="fp64"):
+    """Measured FMA rate of the current GPU in FLOP/s (neno6_pipe_peak):
+    "fp64" (DFMA) or "fp32" (FFMA)."""
+    lib = load_library()
+    v = ctypes.c_double(0.0)
+    rc = lib.neno6_pipe_peak({"fp64": 0, "fp32": 1}[which], ctypes.byref(v), _stream())
+    if rc != OK:
+        raise Neno6Error(rc, "pipe_peak")
+    return v.value
 
 
 class RHS(torch.autograd.Function):
