@@ -176,8 +176,8 @@ cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, do
                                   const uint8_t* net_image, bool bf16, int* status, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const long long tiles = (n + 127) / 128;
-  // the static shared memory (~35 KB with the per-CTA reserve) caps
-  // residency at six CTAs of the SM's 228 KB, so their 64-column TMEM
+  // the static shared memory (~30 KB with the per-CTA reserve) caps
+  // residency at seven CTAs of the SM's 228 KB, so their 64-column TMEM
   // allocations always fit in the 512 columns
   static_assert(kNetImageBytes + kBufXBytes + kBufYBytes + 1024 > 228 * 1024 / 9,
                 "nine resident CTAs would oversubscribe TMEM");

@@ -14,8 +14,8 @@
 //         rows whose logits fall within +-guard_tau of 0 re-evaluated in FP32
 //         on the CUDA cores.
 //
-// Face kernel: persistent CTAs of one warpgroup (five per SM, each with 64
-// TMEM columns).  A block is 64 faces on 4 grid lines: 4 rows x 16
+// Face kernel: persistent CTAs of one warpgroup (six per SM, each with 64
+// TMEM columns, 80 registers per thread and 37 KB of shared memory).  A block is 64 faces on 4 grid lines: 4 rows x 16
 // consecutive x faces, or 4 columns x 16 consecutive y faces.  Per block:
 // stage the 4 x 21 stencil cells (ghost cells by wrap / clamp), compute the
 // 64 Roe states once (one thread per face, FP64) while the other half of the
@@ -63,14 +63,19 @@ constexpr int align_up(int x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr int kOffNet = 0;
 constexpr int kOffBufX = align_up(kOffNet + kNetImageBytes);
 constexpr int kOffBufY = align_up(kOffBufX + kBufXBytes);
-constexpr int kOffCellD = align_up(kOffBufY + kBufYBytes);      // 4 x kMaxCells doubles
-// per cell 8 floats (U_n, F_n deviations interleaved), then per cell 2 floats
-// (normal velocity, sound speed)
-constexpr int kOffCellF = align_up(kOffCellD + 4 * kMaxCells * 8);
+// per cell 8 floats: the (U_n, F_n) deviations, interleaved
+constexpr int kOffCellF = align_up(kOffBufY + kBufYBytes);
+// Between blocks (staging and Roe phase) the operand buffers are free: the
+// layer-2 buffer holds the hand-off of 20 cells' FP64 state (1280 B) and, from
+// byte 2048, the FP64 Roe inputs of every staged cell (4 x kMaxCells doubles);
+// the input-tile buffer holds each cell's FP32 (normal velocity, sound speed).
+constexpr int kCellDInBufX = 2048;
+static_assert(kCellDInBufX >= 20 * 64 && kCellDInBufX + 4 * kMaxCells * 8 <= kBufXBytes, "bufX reuse");
+static_assert(kMaxCells * 8 <= kBufYBytes, "bufY reuse");
 // rows of L/2 for the fields (u_n - c, entropy, u_n + c): kFaces x 12 floats
 // (the shear row of 2D is rebuilt from the Roe velocity); LLF alpha per
 // field: kFaces x 4 floats
-constexpr int kOffL = align_up(kOffCellF + 10 * kMaxCells * 4);
+constexpr int kOffL = align_up(kOffCellF + 8 * kMaxCells * 4);
 constexpr int kOffA = align_up(kOffL + kFaces * 12 * 4);
 constexpr int kOffR = align_up(kOffA + kFaces * 4 * 4);           // kFaces x 5 floats
 constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles + 8 floats
@@ -79,10 +84,10 @@ constexpr int kOffWtab = align_up(kOffBar + 16);    // 16 masks x 4 renormalised
 constexpr int kFacesSmem = align_up(kOffWtab + 16 * 4 * 4);
 // the guard band's per-warp scratch (4 x 128 floats) reuses the layer-2
 // operand buffer, which is free once a batch's MMAs are done.
-// Five CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
+// Six CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
 // plus 1 KB reserved per CTA.
 static_assert(kOffBar % 8 == 0 && kFacesSmem % 128 == 0, "alignment");
-static_assert(5 * (kFacesSmem + 1024) <= 228 * 1024, "face kernel: five CTAs per SM");
+static_assert(6 * (kFacesSmem + 1024) <= 228 * 1024, "face kernel: six CTAs per SM");
 
 // per-cell arrays
 enum { CD_S = 0, CD_U = 1, CD_V = 2, CD_H = 3 };
@@ -249,13 +254,13 @@ __device__ __forceinline__ bool face_valid(const BlockGeom& b, int k, int nx, in
 }
 
 template <int NDIM, bool BF16>
-__global__ void __launch_bounds__(kMlpThreads, 5) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
+__global__ void __launch_bounds__(kMlpThreads, 6) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_net = smem + kOffNet;
-  double* cd = reinterpret_cast<double*>(smem + kOffCellD);
+  double* cd = reinterpret_cast<double*>(smem + kOffBufX + kCellDInBufX);
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
-  float2* cuc = reinterpret_cast<float2*>(cf + 8 * kMaxCells);
+  float2* cuc = reinterpret_cast<float2*>(smem + kOffBufY);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
   float* sA = reinterpret_cast<float*>(smem + kOffA);
   float* ws = reinterpret_cast<float*>(smem + kOffBufX) + (threadIdx.x >> 5) * 128;
@@ -673,9 +678,9 @@ cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
   a.byc = (a.nx + kLines - 1) / kLines;
   a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kLineFaces - 1) / kLineFaces) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
-  // persistent grid: five resident CTAs per SM (registers, shared memory,
+  // persistent grid: six resident CTAs per SM (registers, shared memory,
   // 64 TMEM columns each)
-  const int blocks = (int)(nblk < 152 * 5 ? nblk : 152 * 5);
+  const int blocks = (int)(nblk < 152 * 6 ? nblk : 152 * 6);
   auto kern = ndim == 2 ? (a.bf16 ? faces_mixed_kernel<2, true> : faces_mixed_kernel<2, false>)
                         : (a.bf16 ? faces_mixed_kernel<1, true> : faces_mixed_kernel<1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);

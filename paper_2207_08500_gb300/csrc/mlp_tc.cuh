@@ -14,8 +14,8 @@ namespace tcmlp {
 using namespace tc;
 
 constexpr int kMlpThreads = 128;
-constexpr int kBufXBytes = 128 * 64 * 2;  // A2 (K = 64) / A4
-constexpr int kBufYBytes = 128 * 32 * 2;  // A1 / A3 (K = 32) / A5
+constexpr int kBufXBytes = 128 * 64 * 2;  // A2 (K = 64), then A3 (K = 32), then A4 (K = 16)
+constexpr int kBufYBytes = 128 * 16 * 2;  // A1 (K = 16): the layer-1 input tile
 
 // Round two FP32 values to bf16/fp16 and pack them, a in bits 0-15.
 template <bool BF16>
@@ -133,8 +133,8 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, uint8_
 }
 
 // Layer 3's accumulator row (TMEM columns col3..) + b3 -> ReLU -> 16-bit ->
-// this row of layer 4's operand (K = 16, in bufX, whose layer-2 operand the
-// finished layer-2 MMAs no longer read); layer 4 on the tensor cores (N = 16,
+// this row of layer 4's operand (K = 16, in bufX, whose layer-3 operand the
+// finished layer-3 MMAs no longer read); layer 4 on the tensor cores (N = 16,
 // rows 8-15 of B4 zero) into TMEM columns col4..; its row + b4 -> ReLU, then
 // layer 5 (8 -> 4) in FP32 on the CUDA cores, two outputs per packed FMA (each
 // output accumulates over its inputs in order, one rounding per FMA).
@@ -193,12 +193,12 @@ __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
   if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 16, kNetImageB1, 64, 0);
   wait_layer(c);
   hidden_epilogue<64, BF16>(c, 0, c.bufX);
-  // layer 2 reads the input tile for its bias step before its epilogue
-  // overwrites bufY
+  // layer 2 also reads the input tile (its bias K-step); once its MMAs are
+  // done, its operand buffer takes layer 3's operand
   if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufX, 64, kNetImageB2, 32, 0, kNetImageB2b);
   wait_layer(c);
-  hidden_epilogue<32, BF16>(c, 0, c.bufY);
-  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 32, kNetImageB3, 16, 32);
+  hidden_epilogue<32, BF16>(c, 0, c.bufX);
+  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufX, 32, kNetImageB3, 16, 32);
   wait_layer(c);
   tail_layers<BF16>(c, 32, 48, z);
   // every thread's timeout record is visible after this barrier
