@@ -288,7 +288,7 @@ def run_ours(args, rank, world):
         yt = torch.zeros(n_tr, dtype=torch.uint8, device=dev)
         yt[n_tr // 2:] = 0b1011
         perm = torch.randperm(n_tr, generator=torch.Generator().manual_seed(15)).to(dev, torch.int32)
-        params = torch.from_numpy(oracle_free_init(seed=16)).to(dev)
+        params = torch.from_numpy(he_init_params(seed=16)).to(dev)
         mom = [torch.zeros_like(params), torch.zeros_like(params)]
         g64.mlp_train(Xt, yt, perm[:1750], params, mom[0], mom[1], 0, 1e-4)
         e_a.record(stream)
@@ -384,7 +384,7 @@ def max_over_ranks(values, world, device):
     return vals.tolist()
 
 
-def oracle_free_init(seed):
+def he_init_params(seed):
     """Seeded He-style initial parameters of the 6-64-32-16-8-4 network in
     weights-file order (float32), for the training timing."""
     rng = np.random.default_rng(seed)

@@ -520,7 +520,6 @@ int scalar_check(neno6_handle* h, int law, const void* u, const char* who) {
     return fail(h, NENO6_ERR_ARG, std::string(who) + ": unknown law");
   if (!u) return fail(h, NENO6_ERR_ARG, std::string(who) + ": null pointer");
   if (!aligned(u, 8)) return fail(h, NENO6_ERR_ALIGN, std::string(who) + ": misaligned");
-  if (h->cfg.mask_mode == kMaskGiven) return fail(h, NENO6_ERR_UNSUPPORTED, std::string(who) + ": mask mode");
   return NENO6_OK;
 }
 
