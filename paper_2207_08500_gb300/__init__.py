@@ -24,7 +24,7 @@ LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
 MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
 LAW = {"advection": 0, "burgers": 1}
 # logit band re-evaluated in FP32 by the mixed-precision path
-DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.1}
+DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.5}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
