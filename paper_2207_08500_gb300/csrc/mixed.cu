@@ -4,16 +4,18 @@
 // memory).
 //
 // Tensor-core MLP (one warpgroup per CTA): thread t owns row t of a 128-row
-// batch, which is TMEM lane t and MMA row t.  Layer l's input (128 x K_l, K
-// padded to a multiple of 16) sits in shared memory in the K-major canonical
-// layout of tc.cuh; thread 0 issues the MMAs (D = A * W^T, N = layer width)
-// and commits them to an mbarrier; every thread waits (bounded), loads its
-// row of the FP32 accumulator from TMEM, applies ReLU, rounds to bf16/fp16
-// (one packed cvt per pair) and stores it as its row of the next layer's
-// input.  The biases of layers 1 and 2 are accumulated by the tensor cores
-// (constant-one input columns, see kOnesCol); the biases of layers 3-4 are
-// added in FP32 in the epilogues, and layer 5 (8 -> 4) runs in FP32 on the
-// CUDA cores.  64 TMEM columns per CTA.
+// batch, which is TMEM lane t and MMA row t.  Layer 1's input (128 x 16, K
+// padded) sits in shared memory in the K-major canonical layout of tc.cuh;
+// layers 2-4 read their input from tensor memory, where the previous layer's
+// epilogue writes it (two 16-bit values per 32-bit column) into columns that
+// layer's accumulator has vacated.  Thread 0 issues the MMAs (D = A * W^T,
+// N = layer width) and commits them to an mbarrier; every thread waits
+// (bounded), loads its row of the FP32 accumulator from TMEM, applies ReLU,
+// rounds to bf16/fp16 (one packed cvt per pair) and stores it as its row of
+// the next layer's input.  The biases of layers 1 and 2 are accumulated by
+// the tensor cores (constant-one input columns, see kOnesCol); the biases of
+// layers 3-4 are added in FP32 in the epilogues, and layer 5 (8 -> 4) runs
+// in FP32 on the CUDA cores.  64 TMEM columns per CTA.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -33,6 +35,11 @@ using namespace tcmlp;
 // Batched classifier (neno6_classify, mixed precision): persistent CTAs of
 // 128 threads, one 128-row tile per iteration.  Normalisation (Eq.
 // (normalizainput)) in FP32, then the tensor-core MLP; logit > 0 -> discard.
+// Dynamic shared memory requested at launch and never touched: it keeps a
+// CTA's shared memory at ~30 KB, so that at most seven are resident per SM and
+// their 64-column TMEM allocations always fit in the 512 columns.
+constexpr int kResidencyPad = 16 * 1024;
+
 template <bool BF16>
 __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const double* __restrict__ X,
                                                                       long long n, uint8_t* __restrict__ eta,
@@ -40,7 +47,6 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
                                                                       const uint8_t* __restrict__ net_image,
                                                                       int* status) {
   __shared__ __align__(128) uint8_t s_net[kNetImageBytes];
-  __shared__ __align__(128) uint8_t s_bufX[kBufXBytes];
   __shared__ __align__(128) uint8_t s_bufY[kBufYBytes];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tmem;
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx c{s_net, s_bufX, s_bufY, &s_bar, s_tmem, 0u, BF16, &s_fail};
+  MlpCtx c{s_net, s_bufY, &s_bar, s_tmem, 0u, BF16, &s_fail};
   const long long tiles = (n + 127) / 128;
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long r = tile * 128 + t;
@@ -177,13 +183,15 @@ cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, do
   if (n == 0) return cudaSuccess;
   const long long tiles = (n + 127) / 128;
   // the static shared memory (~30 KB with the per-CTA reserve) caps
-  // residency at seven CTAs of the SM's 228 KB, so their 64-column TMEM
-  // allocations always fit in the 512 columns
-  static_assert(kNetImageBytes + kBufXBytes + kBufYBytes + 1024 > 228 * 1024 / 9,
+  // residency at seven CTAs of the SM's 228 KB (see s_residency_pad)
+  static_assert(kNetImageBytes + kBufYBytes + kResidencyPad + 1024 > 228 * 1024 / 9,
                 "nine resident CTAs would oversubscribe TMEM");
+  static_assert(kNetImageBytes + kBufYBytes + kResidencyPad <= 48 * 1024, "no opt-in needed");
   const int blocks = (int)(tiles < 152 * 6 ? tiles : 152 * 6);
-  if (bf16) classify_mixed_kernel<true><<<blocks, kMlpThreads, 0, s>>>(X, n, eta, logits, net_image, status);
-  else classify_mixed_kernel<false><<<blocks, kMlpThreads, 0, s>>>(X, n, eta, logits, net_image, status);
+  if (bf16)
+    classify_mixed_kernel<true><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image, status);
+  else
+    classify_mixed_kernel<false><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image, status);
   return cudaGetLastError();
 }
 

@@ -14,8 +14,9 @@
 //         rows whose logits fall within +-guard_tau of 0 re-evaluated in FP32
 //         on the CUDA cores.
 //
-// Face kernel: persistent CTAs of one warpgroup (six per SM, each with 64
-// TMEM columns, 80 registers per thread and 37 KB of shared memory).  A block is 64 faces on 4 grid lines: 4 rows x 16
+// Face kernel: persistent CTAs of one warpgroup (eight per SM, each with 64
+// TMEM columns -- all 512 of the SM's -- 64 registers per thread and 26 KB
+// of shared memory; the classifier's hidden activations stay in TMEM).  A block is 64 faces on 4 grid lines: 4 rows x 16
 // consecutive x faces, or 4 columns x 16 consecutive y faces.  Per block:
 // stage the 4 x 21 stencil cells (ghost cells by wrap / clamp), compute the
 // 64 Roe states once (one thread per face, FP64) while the other half of the
@@ -61,17 +62,19 @@ constexpr int kAlign = 128;
 constexpr int align_up(int x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // dynamic shared-memory layout of the face kernel
 constexpr int kOffNet = 0;
-constexpr int kOffBufX = align_up(kOffNet + kNetImageBytes);
-constexpr int kOffBufY = align_up(kOffBufX + kBufXBytes);
+// Scratch: during the staging and Roe phase of a block it holds the hand-off
+// of 20 cells' FP64 state (1280 B) and, from byte 2048, the FP64 Roe inputs of
+// every staged cell (4 x kMaxCells doubles); during the batches the guard
+// band's per-warp rows (4 x 128 floats).  The layer-1 input tile is free
+// between blocks and holds each cell's FP32 (normal velocity, sound speed).
+constexpr int kCellDInScratch = 2048;
+constexpr int kScratchBytes = kCellDInScratch + 4 * kMaxCells * 8;
+static_assert(kCellDInScratch >= 20 * 64 && kCellDInScratch >= 4 * 128 * 4, "scratch layout");
+static_assert(kMaxCells * 8 <= kBufYBytes, "bufY reuse");
+constexpr int kOffScratch = align_up(kOffNet + kNetImageBytes);
+constexpr int kOffBufY = align_up(kOffScratch + kScratchBytes);
 // per cell 8 floats: the (U_n, F_n) deviations, interleaved
 constexpr int kOffCellF = align_up(kOffBufY + kBufYBytes);
-// Between blocks (staging and Roe phase) the operand buffers are free: the
-// layer-2 buffer holds the hand-off of 20 cells' FP64 state (1280 B) and, from
-// byte 2048, the FP64 Roe inputs of every staged cell (4 x kMaxCells doubles);
-// the input-tile buffer holds each cell's FP32 (normal velocity, sound speed).
-constexpr int kCellDInBufX = 2048;
-static_assert(kCellDInBufX >= 20 * 64 && kCellDInBufX + 4 * kMaxCells * 8 <= kBufXBytes, "bufX reuse");
-static_assert(kMaxCells * 8 <= kBufYBytes, "bufY reuse");
 // rows of L/2 for the fields (u_n - c, entropy, u_n + c): kFaces x 12 floats
 // (the shear row of 2D is rebuilt from the Roe velocity); LLF alpha per
 // field: kFaces x 4 floats
@@ -82,12 +85,10 @@ constexpr int kOffRef = align_up(kOffR + kFaces * 5 * 4);         // 8 doubles +
 constexpr int kOffBar = kOffRef + 8 * 8 + 8 * 4;  // mbarrier, TMEM address, timeout flag
 constexpr int kOffWtab = align_up(kOffBar + 16);    // 16 masks x 4 renormalised weights
 constexpr int kFacesSmem = align_up(kOffWtab + 16 * 4 * 4);
-// the guard band's per-warp scratch (4 x 128 floats) reuses the layer-2
-// operand buffer, which is free once a batch's MMAs are done.
-// Six CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
-// plus 1 KB reserved per CTA.
+// Eight CTAs per SM: 228 KB of shared memory, allocated in 128-byte units
+// plus 1 KB reserved per CTA (and 8 x 64 TMEM columns = 512).
 static_assert(kOffBar % 8 == 0 && kFacesSmem % 128 == 0, "alignment");
-static_assert(6 * (kFacesSmem + 1024) <= 228 * 1024, "face kernel: six CTAs per SM");
+static_assert(8 * (kFacesSmem + 1024) <= 228 * 1024, "face kernel: CTAs per SM");
 
 // per-cell arrays
 enum { CD_S = 0, CD_U = 1, CD_V = 2, CD_H = 3 };
@@ -254,16 +255,16 @@ __device__ __forceinline__ bool face_valid(const BlockGeom& b, int k, int nx, in
 }
 
 template <int NDIM, bool BF16>
-__global__ void __launch_bounds__(kMlpThreads, 6) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
+__global__ void __launch_bounds__(kMlpThreads, 8) faces_mixed_kernel(const __grid_constant__ FacesMixedArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* s_net = smem + kOffNet;
-  double* cd = reinterpret_cast<double*>(smem + kOffBufX + kCellDInBufX);
+  double* cd = reinterpret_cast<double*>(smem + kOffScratch + kCellDInScratch);
   float* cf = reinterpret_cast<float*>(smem + kOffCellF);
   float2* cuc = reinterpret_cast<float2*>(smem + kOffBufY);
   float* sL = reinterpret_cast<float*>(smem + kOffL);
   float* sA = reinterpret_cast<float*>(smem + kOffA);
-  float* ws = reinterpret_cast<float*>(smem + kOffBufX) + (threadIdx.x >> 5) * 128;
+  float* ws = reinterpret_cast<float*>(smem + kOffScratch) + (threadIdx.x >> 5) * 128;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 8);
   int* fail_flag = reinterpret_cast<int*>(smem + kOffBar + 12);
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(kMlpThreads, 6) faces_mixed_kernel(const __gri
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  MlpCtx mc{s_net, smem + kOffBufX, smem + kOffBufY, bar, *tmem_slot, 0u, BF16, fail_flag};
+  MlpCtx mc{s_net, smem + kOffBufY, bar, *tmem_slot, 0u, BF16, fail_flag};
   unsigned long long guarded = 0;
   bool failed = false;
 
@@ -339,9 +340,8 @@ __global__ void __launch_bounds__(kMlpThreads, 6) faces_mixed_kernel(const __gri
       cuc[tr] = make_float2(d2f(dir == 0 ? u : v), sqrtf(gamma_f * d2f(p) * d2f(rr)));
       if (tr >= kFaces) {
         // cells kFaces.. are staged by Roe-phase threads: their deviations
-        // are formed by the alpha-phase threads, from the layer-2 operand
-        // buffer (free between blocks)
-        double* sc = reinterpret_cast<double*>(smem + kOffBufX) + (tr - kFaces) * 8;
+        // are formed by the alpha-phase threads, from the scratch
+        double* sc = reinterpret_cast<double*>(smem + kOffScratch) + (tr - kFaces) * 8;
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
           sc[n] = n < NV ? U[n] : 0.0;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kMlpThreads, 6) faces_mixed_kernel(const __gri
       double Uo[4] = {U[0], U[1], NV > 2 ? U[2] : 0.0, NV > 3 ? U[NV - 1] : 0.0};
       deviations(tr, Uo, F);
       if (tr < kMaxCells - kFaces) {
-        const double* sc = reinterpret_cast<const double*>(smem + kOffBufX) + tr * 8;
+        const double* sc = reinterpret_cast<const double*>(smem + kOffScratch) + tr * 8;
         deviations(kFaces + tr, sc, sc + 4);
       }
     }
@@ -678,9 +678,9 @@ cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
   a.byc = (a.nx + kLines - 1) / kLines;
   a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kLineFaces - 1) / kLineFaces) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
-  // persistent grid: six resident CTAs per SM (registers, shared memory,
+  // persistent grid: eight resident CTAs per SM (registers, shared memory,
   // 64 TMEM columns each)
-  const int blocks = (int)(nblk < 152 * 6 ? nblk : 152 * 6);
+  const int blocks = (int)(nblk < 152 * 8 ? nblk : 152 * 8);
   auto kern = ndim == 2 ? (a.bf16 ? faces_mixed_kernel<2, true> : faces_mixed_kernel<2, false>)
                         : (a.bf16 ? faces_mixed_kernel<1, true> : faces_mixed_kernel<1, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kFacesSmem);

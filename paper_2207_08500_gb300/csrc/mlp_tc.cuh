@@ -1,5 +1,12 @@
 // Tensor-core MLP shared by the mixed-precision kernels (see mixed.cu for the
 // scheme): one warpgroup of 128 threads, thread t = MMA row t = TMEM lane t.
+// Layer 1 reads its input tile from shared memory; layers 2-4 read their
+// input (the previous layer's ReLU output rounded to 16 bits) from tensor
+// memory, written there by the epilogue into columns the previous layer's
+// accumulator has vacated.  64 TMEM columns:
+//   layer 1 D [0,64) -> A2 [0,32) (64 values, two per column)
+//   layer 2 D [32,64) -> A3 [0,16);  layer 3 D [16,32) -> A4 [32,40);
+//   layer 4 D [48,64).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -14,8 +21,8 @@ namespace tcmlp {
 using namespace tc;
 
 constexpr int kMlpThreads = 128;
-constexpr int kBufXBytes = 128 * 64 * 2;  // A2 (K = 64), then A3 (K = 32), then A4 (K = 16)
 constexpr int kBufYBytes = 128 * 16 * 2;  // A1 (K = 16): the layer-1 input tile
+constexpr uint32_t kColD1 = 0, kColA2 = 0, kColD2 = 32, kColA3 = 0, kColD3 = 16, kColA4 = 32, kColD4 = 48;
 
 // Round two FP32 values to bf16/fp16 and pack them, a in bits 0-15.
 template <bool BF16>
@@ -68,8 +75,7 @@ __device__ __forceinline__ void store_input_row(uint8_t* bufY, int row, const fl
 
 struct MlpCtx {
   const uint8_t* net;  // shared-memory image (kNetImage* layout)
-  uint8_t* bufX;
-  uint8_t* bufY;
+  uint8_t* bufY;       // layer-1 input tile
   uint64_t* bar;
   uint32_t tmem;
   uint32_t phase;
@@ -96,6 +102,25 @@ __device__ __forceinline__ void issue_layer(const MlpCtx& c, const uint8_t* A, i
   mma_commit(c.bar);
 }
 
+// Issue one layer (thread 0) whose input sits in tensor memory at column
+// colA: K/16 MMAs of K = 16 into column colD, plus, if Bb_off >= 0, the bias
+// K-step on the layer-1 input tile in bufY.
+template <bool BF16>
+__device__ __forceinline__ void issue_layer_t(const MlpCtx& c, uint32_t colA, int K, int B_off, int N,
+                                              uint32_t colD, int Bb_off = -1) {
+  const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+  const uint32_t b0 = smem_u32(c.net + B_off);
+  const uint32_t idesc = idesc_f16(128, N, BF16);
+  tc_fence_after();
+  for (int ks = 0; ks < K / 16; ++ks)
+    mma_f16_ta(c.tmem + colD, c.tmem + colA + 8u * ks, smem_desc(b0 + 256u * ks, 128u, sbo), idesc,
+               ks > 0 ? 1u : 0u);
+  if (Bb_off >= 0)
+    mma_f16(c.tmem + colD, smem_desc(smem_u32(c.bufY), 128u, 256u),
+            smem_desc(smem_u32(c.net + Bb_off), 128u, 256u), idesc, 1u);
+  mma_commit(c.bar);
+}
+
 // Wait for the layer's MMAs (bounded).  A timeout is recorded in the shared
 // flag *fail and acted on, uniformly, at the end of the chain.
 __device__ __forceinline__ void wait_layer(MlpCtx& c) {
@@ -105,17 +130,19 @@ __device__ __forceinline__ void wait_layer(MlpCtx& c) {
 }
 
 // Epilogue of a hidden tensor-core layer (bias already accumulated): this
-// row of the FP32 accumulator -> ReLU -> 16-bit -> this row of the next
-// layer's operand, 32 columns per TMEM round trip.
+// row of the FP32 accumulator at colD -> ReLU -> 16-bit pairs -> this row of
+// the next layer's operand at colA in tensor memory (32 values per round
+// trip).  colA may overlap colD: each 32-value chunk is read before the
+// packed 16 columns are written, and chunk q writes below chunk q+1.
 template <int N, bool BF16>
-__device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, uint8_t* Anext) {
+__device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, uint32_t colD, uint32_t colA) {
   const int t = threadIdx.x;
   const uint32_t lane = (uint32_t)(t & ~31) << 16;
 #pragma unroll
   for (int c32 = 0; c32 < N / 32; ++c32) {
     uint32_t r[16], s[16];
-    tmem_ld16(c.tmem + lane + (uint32_t)(col + 32 * c32), r);
-    tmem_ld16(c.tmem + lane + (uint32_t)(col + 32 * c32 + 16), s);
+    tmem_ld16(c.tmem + lane + colD + 32u * c32, r);
+    tmem_ld16(c.tmem + lane + colD + 32u * c32 + 16u, s);
     tmem_ld_wait();
     uint32_t p[16];
 #pragma unroll
@@ -123,28 +150,26 @@ __device__ __forceinline__ void hidden_epilogue(const MlpCtx& c, int col, uint8_
       p[i] = relu_pack2<BF16>(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
       p[8 + i] = relu_pack2<BF16>(__uint_as_float(s[2 * i]), __uint_as_float(s[2 * i + 1]));
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      st_row8(Anext, t, 32 * c32 + 8 * q, N, p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    tmem_st16(c.tmem + lane + colA + 16u * c32, p);
   }
+  tmem_st_wait();
   tc_fence_before();
-  fence_async_smem();
   __syncthreads();
 }
 
-// Layer 3's accumulator row (TMEM columns col3..) + b3 -> ReLU -> 16-bit ->
-// this row of layer 4's operand (K = 16, in bufX, whose layer-3 operand the
-// finished layer-3 MMAs no longer read); layer 4 on the tensor cores (N = 16,
-// rows 8-15 of B4 zero) into TMEM columns col4..; its row + b4 -> ReLU, then
-// layer 5 (8 -> 4) in FP32 on the CUDA cores, two outputs per packed FMA (each
-// output accumulates over its inputs in order, one rounding per FMA).
+// Layer 3's accumulator row (TMEM columns kColD3..) + b3 -> ReLU -> 16-bit ->
+// this row of layer 4's operand (8 TMEM columns at kColA4); layer 4 on the
+// tensor cores (N = 16, rows 8-15 of B4 zero) into columns kColD4..; its row
+// + b4 -> ReLU, then layer 5 (8 -> 4) in FP32 on the CUDA cores, two outputs
+// per packed FMA (each output accumulates over its inputs in order, one
+// rounding per FMA).
 template <bool BF16>
-__device__ __forceinline__ void tail_layers(MlpCtx& c, int col3, int col4, float z[4]) {
+__device__ __forceinline__ void tail_layers(MlpCtx& c, float z[4]) {
   const int t = threadIdx.x;
   const uint32_t lane = (uint32_t)(t & ~31) << 16;
   const float* bias = reinterpret_cast<const float*>(c.net + kNetImageBias);
   uint32_t r[16];
-  tmem_ld16(c.tmem + lane + (uint32_t)col3, r);
+  tmem_ld16(c.tmem + lane + kColD3, r);
   tmem_ld_wait();
   uint32_t p[8];
 #pragma unroll
@@ -153,14 +178,13 @@ __device__ __forceinline__ void tail_layers(MlpCtx& c, int col3, int col4, float
     const float2 h = __fadd2_rn(make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1])), b);
     p[i] = relu_pack2<BF16>(h.x, h.y);
   }
-  st_row8(c.bufX, t, 0, 16, p[0], p[1], p[2], p[3]);
-  st_row8(c.bufX, t, 8, 16, p[4], p[5], p[6], p[7]);
+  tmem_st8(c.tmem + lane + kColA4, p);
+  tmem_st_wait();
   tc_fence_before();
-  fence_async_smem();
   __syncthreads();
-  if (t == 0) issue_layer<BF16>(c, c.bufX, 16, kNetImageB4, 16, col4);
+  if (t == 0) issue_layer_t<BF16>(c, kColA4, 16, kNetImageB4, 16, kColD4);
   wait_layer(c);
-  tmem_ld16(c.tmem + lane + (uint32_t)col4, r);
+  tmem_ld16(c.tmem + lane + kColD4, r);
   tmem_ld_wait();
   tc_fence_before();
   const float2* W5t = reinterpret_cast<const float2*>(c.net + kNetImageW5);  // [8][2] pairs
@@ -184,23 +208,22 @@ __device__ __forceinline__ void tail_layers(MlpCtx& c, int col3, int col4, float
 
 // The classifier for the 128 rows whose layer-1 inputs are in bufY (K = 16,
 // written by store_input_row): layers 1-4 on the tensor cores, layer 5 on the
-// CUDA cores.  64 TMEM columns: layer 1 -> [0,64); layer 2 -> [0,32) once
-// layer 1's epilogue has read its columns (each epilogue ends with a fence
-// and a barrier before the next issue); layer 3 -> [32,48); layer 4 ->
-// [48,64).  Returns false (uniformly) if an MMA wait timed out.
+// CUDA cores, TMEM columns as listed at the top.  Every epilogue ends with its
+// TMEM stores waited, a fence and a barrier before the next issue, so each
+// layer's MMAs see their whole operand and never overwrite columns a thread
+// is still reading.  Returns false (uniformly) if an MMA wait timed out.
 template <bool BF16>
 __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
-  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 16, kNetImageB1, 64, 0);
+  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufY, 16, kNetImageB1, 64, (int)kColD1);
   wait_layer(c);
-  hidden_epilogue<64, BF16>(c, 0, c.bufX);
-  // layer 2 also reads the input tile (its bias K-step); once its MMAs are
-  // done, its operand buffer takes layer 3's operand
-  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufX, 64, kNetImageB2, 32, 0, kNetImageB2b);
+  hidden_epilogue<64, BF16>(c, kColD1, kColA2);
+  // layer 2 also reads the input tile in bufY (its bias K-step)
+  if (threadIdx.x == 0) issue_layer_t<BF16>(c, kColA2, 64, kNetImageB2, 32, kColD2, kNetImageB2b);
   wait_layer(c);
-  hidden_epilogue<32, BF16>(c, 0, c.bufX);
-  if (threadIdx.x == 0) issue_layer<BF16>(c, c.bufX, 32, kNetImageB3, 16, 32);
+  hidden_epilogue<32, BF16>(c, kColD2, kColA3);
+  if (threadIdx.x == 0) issue_layer_t<BF16>(c, kColA3, 32, kNetImageB3, 16, kColD3);
   wait_layer(c);
-  tail_layers<BF16>(c, 32, 48, z);
+  tail_layers<BF16>(c, z);
   // every thread's timeout record is visible after this barrier
   return __syncthreads_or(*c.fail) == 0;
 }
