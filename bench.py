@@ -363,7 +363,7 @@ def run_ours(args, rank, world):
 # capture of the current kernels at 2048^2 (profiles/*.md), scaled by cells
 # for other grids (the traffic is U once, the face fluxes once and the halo
 # re-reads, all proportional to the cells)
-TRAFFIC_2048 = {True: 141.2e6 + 96.6e6, False: 270.8e6 + 232.8e6}
+TRAFFIC_2048 = {True: 141.2e6 + 96.6e6, False: 287.6e6 + 236.8e6}
 TRAFFIC_NOTE = {True: "rhs_fp64_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
                       "capture at 2048^2, scaled by cells",
                 False: "faces_mixed_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
