@@ -16,8 +16,9 @@
 //
 // Face kernel: persistent CTAs of one warpgroup (eight per SM, each with 64
 // TMEM columns -- all 512 of the SM's -- 64 registers per thread and 26 KB
-// of shared memory; the classifier's hidden activations stay in TMEM).  A block is 64 faces on 4 grid lines: 4 rows x 16
-// consecutive x faces, or 4 columns x 16 consecutive y faces.  Per block:
+// of shared memory; the classifier's hidden activations stay in TMEM).  A
+// block is 64 faces on 4 grid lines: 4 rows x 16 consecutive x faces, or 4
+// columns x 16 consecutive y faces.  Per block:
 // stage the 4 x 21 stencil cells (ghost cells by wrap / clamp), compute the
 // 64 Roe states once (one thread per face, FP64) while the other half of the
 // CTA forms the LLF alpha of every (face, field), then four 128-row
