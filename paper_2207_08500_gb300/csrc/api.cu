@@ -389,8 +389,11 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
   }
   double* S1 = h->d_stage;
   double* S2 = h->d_stage + h->state_elems;
-  cudaError_t e = launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
-                                    h->d_status, s);
+  cudaError_t e = h->cfg.precision == NENO6_FP64
+                      ? launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
+                                          h->d_status, s)
+                      : launch_cfl_mixed(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
+                                         h->d_status, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step: cfl reduction");
   if (h->cfg.precision != NENO6_FP64) {
     double* tp = t_dev ? t_dev : h->d_t;

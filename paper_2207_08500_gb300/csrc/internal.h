@@ -118,6 +118,8 @@ struct DiffArgs {
 
 cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s);
 cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s);
+cudaError_t launch_cfl_mixed(int ndim, const double* U, int nx, int ny, double gamma, unsigned long long* smax,
+                             int* status, cudaStream_t s);
 cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, double dy, double cfl, double t_end,
                       const double* t_dev, double* dt_dev, double* dt_user, cudaStream_t s);
 

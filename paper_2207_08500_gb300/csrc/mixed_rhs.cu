@@ -644,6 +644,48 @@ __global__ void __launch_bounds__(256) diff_mixed_kernel(DiffArgs a) {
   }
 }
 
+// Largest wave speeds max(|u|+c), max(|v|+c) of the mixed path's step (Sec.
+// 4.4's CFL condition): the pressure, whose difference E - rho|u|^2/2 cancels
+// at high Mach numbers, in FP64 (reciprocal of rho by the hardware
+// approximation and one Newton step); velocities and sound speed in FP32.
+// The step size only has to respect the CFL bound, and a relative error of
+// ~1e-7 in it changes nothing else: the RK3 accumulation stays FP64.  The
+// maxima are handed to dt_kernel as binary64 bit patterns, like the FP64
+// path's (non-negative values order like their patterns).
+template <int NDIM>
+__global__ void __launch_bounds__(256) cfl_mixed_kernel(const double* __restrict__ U, int nx, int ny,
+                                                        double gamma, unsigned long long* smax, int* status) {
+  const size_t plane = (size_t)nx * ny;
+  const double gm1 = gamma - 1.0;
+  const float gamma_f = (float)gamma;
+  float mx = 0.0f, my = 0.0f;
+  bool bad = false;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const double rho = U[k];
+    const double m = U[plane + k];
+    const double n = NDIM == 2 ? U[2 * plane + k] : 0.0;
+    const double E = U[(NDIM == 2 ? 3 : 2) * plane + k];
+    const double rr = rcp64(rho);
+    const double p = gm1 * fma(-0.5 * rr, fma(n, n, m * m), E);
+    bad |= !positive64(rho) || !positive64(p);
+    const float rf = d2f(rr);
+    const float c = sqrtf(gamma_f * d2f(p) * rf);
+    mx = fmaxf(mx, fabsf(d2f(m) * rf) + c);
+    if (NDIM == 2) my = fmaxf(my, fabsf(d2f(n) * rf) + c);
+  }
+  if (bad) atomicOr(status, 1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&smax[0], (unsigned long long)__double_as_longlong(f2d(mx)));
+    if (NDIM == 2) atomicMax(&smax[1], (unsigned long long)__double_as_longlong(f2d(my)));
+  }
+}
+
 // dt = cfl / (max(|u|+c)/dx + max(|v|+c)/dy), clipped to t_end (one thread).
 __global__ void dt_kernel(const unsigned long long* smax, int ndim, double dx, double dy, double cfl,
                           double t_end, const double* t_dev, double* dt_dev, double* dt_user) {
@@ -694,6 +736,18 @@ cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s) {
   const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535));
   if (ndim == 2) diff_mixed_kernel<2><<<grid, 256, 0, s>>>(a);
   else diff_mixed_kernel<1><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_mixed(int ndim, const double* U, int nx, int ny, double gamma, unsigned long long* smax,
+                             int* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const size_t cells = (size_t)nx * ny;
+  unsigned blocks = (unsigned)((cells + 255) / 256);
+  if (blocks > 152u * 8u) blocks = 152u * 8u;
+  if (ndim == 2) cfl_mixed_kernel<2><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
+  else cfl_mixed_kernel<1><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
   return cudaGetLastError();
 }
 

