@@ -61,6 +61,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=20220717)
     ap.add_argument("--threads", type=int, default=2)
+    ap.add_argument("--widths", default="6,64,32,16,8,4",
+                    help="layer widths, inputs first (Sec. 3.1: 6,64,32,16,8,4)")
     ap.add_argument("--out", default="weights/neno6_mlp_6x64x32x16x8x4.bin")
     ap.add_argument("--log", default="weights/train_log.txt")
     args = ap.parse_args()
@@ -71,15 +73,15 @@ def main():
     ytr_t = torch.from_numpy(ytr.astype(np.float32))
     Xva_t = torch.from_numpy(Xva.astype(np.float32))
     yva_t = torch.from_numpy(yva.astype(np.float32))
-    model = make_model()
+    model = make_model(tuple(int(w) for w in args.widths.split(",")))
     opt = torch.optim.Adam(model.parameters(), lr=args.lr)
     sched = torch.optim.lr_scheduler.MultiStepLR(opt, milestones=list(MILESTONES), gamma=0.5)
     bce = torch.nn.BCEWithLogitsLoss()  # mean over outputs and batch = Eq. (Crossentropy)
     gen = torch.Generator().manual_seed(args.seed)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     with open(args.log, "a") as lf:
-        lf.write("# samples %d (train %d, val %d), batch %d, lr %g, milestones %s\n"
-                 % (args.samples, len(Xtr), len(Xva), args.batch, args.lr, MILESTONES))
+        lf.write("# samples %d (train %d, val %d), batch %d, lr %g, milestones %s, widths %s\n"
+                 % (args.samples, len(Xtr), len(Xva), args.batch, args.lr, MILESTONES, args.widths))
     for ep in range(1, args.epochs + 1):
         t0 = time.time()
         model.train()
