@@ -507,3 +507,34 @@ def test_jvp_cells_equal_full_jvp(oracle_mod, bc):
     cells = np.array([0, 5, nx - 1, nx, 4 * nx + 6, nx * ny - 1, nx * (ny - 1)])
     got = o.jvp_cells(U, V, mask, cells)
     assert np.array_equal(got, jv.reshape(4, -1)[:, cells].T)
+
+
+# ------------------------------------------------------------ scalar Burgers
+def test_burgers_conservation_max_principle_and_shock_speed(oracle_mod):
+    """Sec. 4.2 (Burgers, f = u^2/2) in the oracle's scalar solve:
+    * periodic grid: sum(u) is conserved to round-off by the conservative
+      difference, with the network's masks;
+    * every stencil discarded: the scheme is first-order LLF, which is
+      monotone at CFL 0.4, so the solution stays within [min u0, max u0];
+    * Riemann data u_L = 2, u_R = 0 (transmissive): the shock moves at the
+      Rankine-Hugoniot speed (u_L + u_R)/2 = 1; after t = 0.15 the level
+      u = 1 is crossed within two cells of x_0 + 0.15."""
+    import os
+    from oracle.weights import Net
+    n = 200
+    x = (np.arange(n) + 0.5) / n
+    u0 = np.sin(2 * math.pi * x) + 0.3 * np.where((x > 0.3) & (x < 0.6), 1.0, 0.0)
+    # the trained classifier (a random one keeps stencils across the jumps)
+    net = Net.load(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "weights", "neno6_mlp_6x64x32x16x8x4.bin"))
+    o = oracle_mod.Oracle(ndim=1, nx=n, dx=1.0 / n, net=net)
+    u, _ = o.scalar_solve(1, u0, 0.4, 0.3)
+    assert abs(u.sum() - u0.sum()) <= 1e-12 * np.abs(u0).sum()
+    r, _ = o.scalar_solve(1, u0, 0.4, 0.3, mask_mode="rough")
+    assert r.min() >= u0.min() - 1e-14 and r.max() <= u0.max() + 1e-14
+    ob = oracle_mod.Oracle(ndim=1, nx=n, dx=1.0 / n, bc=("transmissive", "transmissive"), net=net)
+    ur = np.where(x < 0.3, 2.0, 0.0)
+    for mode in ("mlp", "rough"):
+        v, _ = ob.scalar_solve(1, ur, 0.4, 0.15, mask_mode=mode)
+        xs = x[np.argmax(v < 1.0)]
+        assert abs(xs - 0.45) <= 2.0 / n, (mode, xs)
