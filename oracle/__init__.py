@@ -10,10 +10,9 @@ numpy arrays.  Candidate coefficients and linear weights come from
 coefficients.py (exact rational derivation), the classifier parameters from
 weights.py.
 
-Parity status of each part is recorded in the design doc; everything here is pinned
-by tests/test_oracle_*.py except the trained classifier weights themselves
-(the paper's network is not available), whose masks are "parity unpinned"
-against the paper.
+Parity status: everything here is pinned by tests/test_oracle_*.py except
+the trained classifier weights themselves (the paper's network is not
+available), whose masks are "parity unpinned" against the paper.
 """
 import ctypes
 import os

@@ -35,7 +35,7 @@
 // makes the oracle a deterministic function of its inputs on any IEEE-754
 // machine.
 //
-// Readings of the paper where it is silent (each is listed in the design doc):
+// Readings of the paper where it is silent:
 //   - negative-side stencil: the mirror image about x_{i+1/2},
 //     (g-_{i+3}, ..., g-_{i-2}), through the same network and coefficients;
 //   - first-order upwind fallback: g+_{m,i} for the "+" side, g-_{m,i+1} for

@@ -15,7 +15,7 @@ Training infrastructure (oracle side).  For each sample:
                                         labeler Sec. 3.2 names for data whose
                                         regularity is not known in closed form.
 
-Readings where Table 9 is under-specified (listed in the design doc): a_k ~
+Readings where Table 9 is under-specified: a_k ~
 U[0.1, 2] in family 2; the "0.6" of N[0, 0.6] in family 5 is a variance;
 family 6 joins (x-a1)^k1 and (x-a2)^k2 (integer k in 2..8) continuously at a
 kink x_k ~ U[-0.6, 0.6]; family 8 places the jump at the sampled interface
