@@ -107,3 +107,25 @@ def test_mixed_classify_close_to_fp64(lib, tmp_path):
     e16 = lib.Neno6(ndim=1, nx=8, precision="bf16", weights=str(path)).classify(X).cpu().numpy()
     flips = np.unpackbits(e64 ^ e16).sum() / (4 * len(e64))
     assert flips < 0.02, flips
+
+
+@pytest.mark.parametrize("kind", ["fp16", "bf16"])
+def test_width_study_emulation_matches_kernel(lib, kind):
+    """The host emulation the width study uses (oracle/train/width_study.py)
+    against the tensor-core kernel on the trained network: per-row logits
+    agree to the emulation's own tolerance, and the logit errors against FP64
+    have the same distribution on both sides."""
+    from oracle.train import width_study as ws
+    from oracle.weights import Net
+    net = Net.load(lib.DEFAULT_WEIGHTS)
+    g = lib.Neno6(ndim=1, nx=8, precision=kind, guard_tau=0.0)
+    X = synth.mlp_stencils(1 << 16, seed=31)
+    _, z = g.classify(torch.from_numpy(X).cuda(), want_logits=True)
+    z = z.cpu().numpy()
+    ze = ws.forward16(net, X, kind).astype(np.float64)
+    z64 = ws.forward64(net, X)
+    err = np.abs(z - ze) / (1.0 + np.abs(ze))
+    assert np.quantile(err, 0.999) < (2e-2 if kind == "bf16" else 3e-3)
+    q_kernel = np.quantile(np.abs(z - z64), [0.5, 0.99])
+    q_emul = np.quantile(np.abs(ze - z64), [0.5, 0.99])
+    np.testing.assert_allclose(q_kernel, q_emul, rtol=0.2)
