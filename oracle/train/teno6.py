@@ -54,16 +54,22 @@ def beta_matrix(offsets):
 def _beta(F, offsets):
     B = beta_matrix(tuple(offsets))
     cols = [o + 2 for o in offsets]  # position in the six-point stencil
-    V = F[:, cols]
+    # beta does not change when a constant is added to every value (the
+    # derivatives of p do not), so the first value is subtracted first: a
+    # constant sub-stencil then gives exactly 0, as in exact arithmetic,
+    # instead of rounding noise that eps = 1e-40 would magnify
+    V = F[:, cols] - F[:, cols[:1]]
     return np.einsum("ni,ij,nj->n", V, B, V)
 
 
 def smoothness(F):
-    """beta_0..beta_3 and beta_6 of stencils F [n, 6] (values at i-2..i+3)."""
+    """beta_0..beta_3 and beta_6 of stencils F [n, 6] (values at i-2..i+3).
+    Each is an integral of squared derivatives, so never negative; a
+    quadratic form that rounds below 0 is taken as 0."""
     F = np.asarray(F, dtype=np.float64)
     b = np.stack([_beta(F, STENCILS[k]) for k in range(4)], axis=1)
     b6 = _beta(F, FULL)
-    return b, b6
+    return np.maximum(b, 0.0), np.maximum(b6, 0.0)
 
 
 def select(F):
