@@ -1,0 +1,88 @@
+"""Pins of the training-data generator (oracle/train/datagen.py; Algorithm 1,
+Table 9 and Eq. (normalizainput)): the geometric labels against a
+cell-by-cell brute force, and the labels of the generated samples against
+what their function families fix (a jump family's kept sub-stencils are
+constant and its discarded ones are not; a kink family's kept sub-stencils
+lie on one line; smooth families keep everything)."""
+import numpy as np
+
+from oracle.train import datagen
+
+# positions (0..5 = cells i-2..i+3) of each candidate sub-stencil S_k
+CELLS = {0: (1, 2, 3), 1: (2, 3, 4), 2: (0, 1, 2), 3: (2, 3, 4, 5)}
+
+
+def brute_geometric(x_i, dx, sing):
+    eta = np.zeros(4, dtype=np.uint8)
+    centres = x_i + (np.arange(6) - 2) * dx
+    for k, cells in CELLS.items():
+        lo, hi = centres[cells[0]], centres[cells[-1]]
+        eta[k] = any(lo < s < hi for s in sing)
+    return eta
+
+
+def test_geometric_labels_brute_force():
+    rng = np.random.default_rng(3)
+    n = 400
+    x_i = rng.uniform(-1, 1, n)
+    dx = rng.choice([0.01, 0.02, 0.04], n)
+    sing = x_i[:, None] + rng.uniform(-3.5, 4.5, (n, 3)) * dx[:, None]
+    valid = rng.uniform(size=(n, 3)) < 0.7
+    eta = datagen._geometric(x_i, dx, sing, valid)
+    for r in range(n):
+        assert eta[r].tolist() == brute_geometric(x_i[r], dx[r], sing[r][valid[r]]).tolist()
+    # a singular point at the face x_{i+1/2}: S_0, S_1, S_3 cross it, S_2 does not
+    e = datagen._geometric(np.array([0.0]), np.array([0.1]), np.array([[0.05]]), np.array([[True]]))
+    assert e.tolist() == [[1, 1, 0, 1]]
+
+
+def _gen(n=20000, seed=11):
+    return datagen.generate(n, seed=seed)
+
+
+def test_shapes_normalisation_and_smooth_families():
+    X, eta, fam = _gen()
+    assert X.shape == (20000, 6) and eta.shape == (20000, 4) and set(np.unique(fam)) == set(range(1, 10))
+    assert np.abs(X).max() <= 1.0
+    # Eq. (normalizainput): rows whose largest |value| reached 1 or more now peak at exactly 1
+    big = np.abs(X).max(axis=1) == 1.0
+    assert big.mean() > 0.3
+    assert (eta[fam <= 3] == 0).all()
+
+
+def test_jump_family_labels_match_its_values():
+    X, eta, fam = _gen()
+    m = np.flatnonzero(fam == 8)
+    assert len(m) > 1000
+    for r in m:
+        levels = np.unique(X[r])
+        assert len(levels) <= 2
+        for k, cells in CELLS.items():
+            constant = np.ptp(X[r, list(cells)]) == 0.0
+            assert constant == (eta[r, k] == 0), (X[r], eta[r])
+    # every sample's stencil holds the jump (at the interface or another face)
+    assert (eta[m].sum(axis=1) > 0).all()
+
+
+def test_kink_family_kept_stencils_are_linear():
+    X, eta, fam = _gen()
+    for r in np.flatnonzero(fam == 5):
+        scale = max(np.abs(X[r]).max(), 1e-300)
+        for k, cells in CELLS.items():
+            if eta[r, k] == 0:
+                v = X[r, list(cells)]
+                d2 = v[:-2] - 2 * v[1:-1] + v[2:]
+                assert np.abs(d2).max() <= 1e-12 * scale, (X[r], eta[r], k)
+
+
+def test_sign_symmetry_and_split():
+    X, eta, fam = _gen()
+    # family 3 (a Gaussian, positive everywhere) is negated for about half the samples
+    m = fam == 3
+    neg = (X[m] < 0).all(axis=1)
+    pos = (X[m] > 0).all(axis=1)
+    assert (neg | pos).all()
+    n3 = m.sum()
+    assert abs(neg.sum() - n3 / 2) < 5 * np.sqrt(n3 / 4)
+    (Xt, yt), (Xv, yv), _ = datagen.dataset(n_total=1000, seed=5)
+    assert len(Xt) == 700 and len(Xv) == 300
