@@ -150,6 +150,24 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
                double* dt_dev, void* stream);
 
 /*
+ * neno6_step_host — the same SSP-RK3 step (Sec. 4.4) on a state held in
+ * HOST memory: copies U_in to a library-owned device state, runs neno6_step
+ * on it, copies the result to U_out and synchronises the stream before
+ * returning.
+ *   U_in   [nv][ny][nx] float64 host array (pinned memory makes the copies
+ *          asynchronous DMA; pageable memory works too, more slowly).
+ *   U_out  [nv][ny][nx] float64 host array; may be U_in.
+ *   t_io   nullable host float64: t in, t + dt out (t_end clips as in
+ *          neno6_step).  When NULL the handle's internal time is used.
+ * The device state (nv * nx * ny doubles) is allocated on the first call and
+ * kept by the handle.  Device-side conditions (non-physical states) are
+ * latched in the status word as for neno6_step.
+ * Errors: ARG, CUDA.
+ */
+int neno6_step_host(neno6_handle* h, const double* U_in, double* U_out, double cfl, double t_end,
+                    double* t_io, void* stream);
+
+/*
  * neno6_classify — the classifier alone on a batch of stencils: Eq.
  * (normalizainput) then Eqs. (reconstuction), (activationfunction); eta_k =
  * [logit_k > 0] (sigmoid > 1/2, Sec. 3.1).

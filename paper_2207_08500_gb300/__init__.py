@@ -28,7 +28,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.5}
 
 # Public C symbols declared in include/neno6.h (checked by the tests).
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
-           "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
+           "neno6_step_host", "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
            "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train",
            "neno6_scalar_rhs", "neno6_scalar_solve", "neno6_pipe_peak")
 
@@ -66,6 +66,8 @@ def load_library(path=LIB_PATH):
     lib.neno6_mask_bytes.restype = i64
     lib.neno6_rhs.argtypes = [vp, dp, dp, u8p, u8p, vp]
     lib.neno6_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp, dp, vp]
+    lib.neno6_step_host.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_double), vp]
     lib.neno6_classify.argtypes = [vp, dp, i64, u8p, dp, vp]
     lib.neno6_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     lib.neno6_last_error.argtypes = [vp]
@@ -184,6 +186,25 @@ class Neno6:
         self._check(self._lib.neno6_step(self._h, _ptr(U), float(cfl), float(t_end), _ptr(t),
                                          _ptr(dt), _stream()))
         return U
+
+    def step_host(self, U_host, cfl, t_end=0.0, t=None, out=None):
+        """One SSP-RK3 step of a state in host memory (float64 CPU tensor
+        [nv, ny, nx], pinned for asynchronous copies): the library copies it
+        to the device, steps it and copies the result to `out` (default: a
+        new CPU tensor; may be U_host).  t: optional float time, returned
+        advanced by dt.  Returns (out, t)."""
+        assert not U_host.is_cuda and U_host.dtype == torch.float64
+        if not (U_host.is_contiguous() and tuple(U_host.shape) == self.shape):
+            raise ValueError("U_host must be a contiguous float64 CPU tensor of shape %s" % (self.shape,))
+        if out is None:
+            out = torch.empty_like(U_host)
+        assert not out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+        assert tuple(out.shape) == self.shape
+        tc = None if t is None else ctypes.c_double(float(t))
+        self._check(self._lib.neno6_step_host(self._h, _ptr(U_host), _ptr(out), float(cfl),
+                                              float(t_end), None if tc is None else ctypes.byref(tc),
+                                              _stream()))
+        return out, (None if tc is None else tc.value)
 
     def classify(self, X, want_logits=False):
         """Classifier bits (and logits) of raw stencils X [n, 6] float64."""

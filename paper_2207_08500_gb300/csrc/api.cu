@@ -27,6 +27,7 @@ struct neno6_handle {
   double* d_dt = nullptr;     // dt of the current step
   double* d_t = nullptr;      // internal time (neno6_step with t_dev == NULL)
   double* d_stage = nullptr;  // two RK3 stage states (lazily allocated)
+  double* d_host_state = nullptr;  // device copy of neno6_step_host's state (lazily)
   uint8_t* d_net_image = nullptr;  // tensor-core classifier image (mixed precision)
   float* d_guard_w = nullptr;      // FP32 transposed parameters (guard band)
   double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
@@ -325,6 +326,7 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_dt);
   cudaFree(h->d_t);
   cudaFree(h->d_stage);
+  cudaFree(h->d_host_state);
   cudaFree(h->d_net_image);
   cudaFree(h->d_guard_w);
   cudaFree(h->d_faces);
@@ -426,6 +428,39 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
     e = launch_rhs_fp64(h->cfg.ndim, p, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "step: stage launch");
   }
+  return NENO6_OK;
+}
+
+int neno6_step_host(neno6_handle* h, const double* U_in, double* U_out, double cfl, double t_end,
+                    double* t_io, void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (!U_in || !U_out) return fail(h, NENO6_ERR_ARG, "step_host: null state pointer");
+  if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step_host: need cfl > 0, t_end >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = h->state_elems * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (!h->d_host_state) {
+    // the state, then the caller's time (kept apart from the internal time)
+    e = cudaMalloc(&h->d_host_state, bytes + 2 * sizeof(double));
+    if (e != cudaSuccess) {
+      h->d_host_state = nullptr;
+      return cuda_fail(h, e, "step_host: device state");
+    }
+  }
+  double* t_dev = t_io ? h->d_host_state + h->state_elems : nullptr;
+  e = cudaMemcpyAsync(h->d_host_state, U_in, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && t_io) e = cudaMemcpyAsync(t_dev, t_io, sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host: copy in");
+  const int rc = neno6_step(h, h->d_host_state, cfl, t_end, t_dev, nullptr, stream);
+  if (rc != NENO6_OK) {
+    cudaStreamSynchronize(s);  // the copy in reads U_in: finish it before returning
+    return rc;
+  }
+  e = cudaMemcpyAsync(U_out, h->d_host_state, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && t_io) e = cudaMemcpyAsync(t_io, t_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host: copy out");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host: synchronise");
   return NENO6_OK;
 }
 
