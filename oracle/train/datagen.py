@@ -33,6 +33,8 @@ the FP64 oracle).  Here the family-8 levels are drawn from U[-2, 2] and every
 sample is negated with probability 1/2 (a function and its negative have the
 same singular points and the same TENO6 selection, so the labels are kept).
 """
+import math
+
 import numpy as np
 
 from . import teno6
@@ -130,6 +132,112 @@ def generate(n, seed=20220717):
     # Eq. (normalizainput)
     Xn = F / np.maximum(np.abs(F).max(axis=1, keepdims=True), 1.0)
     return Xn, eta, fam
+
+
+# Columns of a uniform draw matrix u [n][DRAWS] (values in [0, 1)) for
+# from_uniforms: grid, family, interface position, five family parameters,
+# sign.
+DRAWS = 9
+
+
+def _ipow(b, k):
+    r = b
+    for _ in range(k - 1):
+        r = r * b
+    return r
+
+
+def from_uniforms(u):
+    """The recipe of `generate` (Table 9, Algorithm 1, the readings above) as
+    a plain function of caller-given uniform draws u [n][DRAWS], one sample
+    per row, in IEEE binary64 without fused operations: the form a device
+    generator can reproduce from the same draws.  (`generate`, which wrote
+    the frozen weights, draws from numpy's generator in its own order and
+    maps some parameters differently, e.g. the normal of family 5; the two
+    produce the same distribution, not the same samples.)
+
+    Returns (Xn [n][6] float64 normalised by Eq. (normalizainput),
+    labels [n] uint8 with eta_k in bit k, fam [n] uint8)."""
+    u = np.asarray(u, dtype=np.float64)
+    assert u.ndim == 2 and u.shape[1] == DRAWS
+    n = u.shape[0]
+    F = np.zeros((n, 6))
+    eta = np.zeros((n, 4), dtype=np.uint8)
+    fam = np.zeros(n, dtype=np.uint8)
+    two_pi = 2.0 * math.pi
+    for r in range(n):
+        q = [float(v) for v in u[r]]
+        N = 50 if q[0] < 0.4 else (100 if q[0] < 0.8 else 200)
+        f = 1 + min(int(9.0 * q[1]), 8)
+        i = 2 + min(int((N - 5) * q[2]), N - 6)
+        p = q[3:8]
+        dx = 2.0 / N
+        xi = -1.0 + (i + 0.5) * dx
+        X = [xi + (j - 2) * dx for j in range(6)]
+        sing = []       # singular points (families 4-8 except 4)
+        period = None   # family 4: kinks at every multiple of P
+        if f == 1:
+            k = -5.0 + 10.0 * p[0]
+            v = [k * x for x in X]
+        elif f == 2:
+            a, k = 0.1 + 1.9 * p[0], 1.0 + 4.0 * p[1]
+            v = [a * math.sin(k * x) for x in X]
+        elif f == 3:
+            a1, a2 = -1.0 + 2.0 * p[0], -1.0 + 2.0 * p[1]
+            v = [math.exp(a1 * ((x - a2) * (x - a2))) for x in X]
+        elif f == 4:
+            rr, P = 1.0 + 2.0 * p[0], (2.0 + 6.0 * p[1]) * dx
+            v = []
+            for x in X:
+                md = x - (2.0 * P) * math.floor(x / (2.0 * P))
+                v.append((rr / P) * (P - abs(md - P)))
+            period = P
+        elif f == 5:
+            b1 = math.sqrt(0.6) * (math.sqrt(-2.0 * math.log(1.0 - p[0])) * math.cos(two_pi * p[1]))
+            x0, c = -0.6 + 1.2 * p[2], p[3]
+            v = [max(0.0, b1 * (x - x0)) + c for x in X]
+            sing = [x0]
+        elif f == 6:
+            k1, k2 = 2 + min(int(7.0 * p[0]), 6), 2 + min(int(7.0 * p[1]), 6)
+            a1, a2, xk = 2.0 * p[2], 2.0 * p[3], -0.6 + 1.2 * p[4]
+            jump = _ipow(xk - a1, k1) - _ipow(xk - a2, k2)
+            v = [_ipow(x - a1, k1) if x <= xk else _ipow(x - a2, k2) + jump for x in X]
+            sing = [xk]
+        elif f == 7:
+            al, a = 0.05 + 1.95 * p[0], 2.0 * p[1]
+            v = [math.sqrt(max(0.0, 1.0 - (al * al) * ((x - a) * (x - a)))) for x in X]
+            sing = [a - 1.0 / al, a + 1.0 / al]
+        elif f == 8:
+            xl, xr = -2.0 + 4.0 * p[0], -2.0 + 4.0 * p[1]
+            shift = 0 if p[2] < 0.5 else -2 + min(int(5.0 * p[3]), 4)
+            xj = xi + (0.5 + shift) * dx
+            v = [xl if x <= xj else xr for x in X]
+            sing = [xj]
+        else:
+            a1, x0, Nf = 2.0 * p[0], 2.0 * p[1], (0.125 + 0.375 * p[2]) * N
+            v = [a1 * math.sin((Nf * math.pi) * (x - x0)) for x in X]
+        F[r] = v
+        fam[r] = f
+        if 4 <= f <= 8:
+            for k, (lo_o, hi_o) in SPAN.items():
+                lo, hi = xi + lo_o * dx, xi + hi_o * dx
+                if period is not None:  # is some multiple m P strictly inside?
+                    hit = False
+                    m = math.floor(lo / period)
+                    while m * period < hi:
+                        hit = hit or m * period > lo
+                        m += 1
+                else:
+                    hit = any(lo < s_ < hi for s_ in sing)
+                eta[r, k] = 1 if hit else 0
+    m9 = fam == 9
+    if m9.any():
+        eta[m9] = teno6.labels(F[m9])
+    neg = u[:, 8] < 0.5
+    F[neg] = -F[neg]
+    Xn = F / np.maximum(np.abs(F).max(axis=1, keepdims=True), 1.0)
+    labels = (eta.astype(np.uint8) << np.arange(4, dtype=np.uint8)).sum(axis=1).astype(np.uint8)
+    return Xn, labels, fam
 
 
 def dataset(n_total=709000, seed=20220717):

@@ -86,3 +86,47 @@ def test_sign_symmetry_and_split():
     assert abs(neg.sum() - n3 / 2) < 5 * np.sqrt(n3 / 4)
     (Xt, yt), (Xv, yv), _ = datagen.dataset(n_total=1000, seed=5)
     assert len(Xt) == 700 and len(Xv) == 300
+
+
+def _from_uniforms(n=20000, seed=12):
+    u = np.random.default_rng(seed).random((n, datagen.DRAWS))
+    X, labels, fam = datagen.from_uniforms(u)
+    eta = ((labels[:, None] >> np.arange(4)) & 1).astype(np.uint8)
+    return u, X, eta, fam
+
+
+def test_from_uniforms_labels_match_values():
+    u, X, eta, fam = _from_uniforms()
+    assert set(np.unique(fam)) == set(range(1, 10)) and np.abs(X).max() <= 1.0
+    assert (eta[fam <= 3] == 0).all()
+    for r in np.flatnonzero(fam == 8):
+        for k, cells in CELLS.items():
+            assert (np.ptp(X[r, list(cells)]) == 0.0) == (eta[r, k] == 0)
+    # families 4 (triangle wave) and 5 (ramp): piecewise linear, so a
+    # sub-stencil is kept iff its values lie on one line (up to rounding)
+    for f in (4, 5):
+        for r in np.flatnonzero(fam == f):
+            scale = np.abs(X[r]).max()
+            for k, cells in CELLS.items():
+                v = X[r, list(cells)]
+                d2 = np.abs(v[:-2] - 2 * v[1:-1] + v[2:]).max()
+                if eta[r, k] == 0:
+                    assert d2 <= 1e-12 * scale
+                elif f == 4:
+                    assert d2 > 1e-9 * scale, (X[r], eta[r], k)
+
+
+def test_from_uniforms_same_distribution_as_generate():
+    _, _, eta, fam = _from_uniforms(30000, seed=13)
+    _, y, fam_g = datagen.generate(30000, seed=14)
+    for f in range(1, 10):
+        assert abs((fam == f).mean() - 1 / 9) < 0.01
+        a, b = eta[fam == f].mean(axis=0), y[fam_g == f].mean(axis=0)
+        assert np.abs(a - b).max() < 0.03, (f, a, b)
+
+
+def test_from_uniforms_edges_of_the_draws():
+    # the smallest and largest draws map inside every range
+    u = np.array([[0.0] * datagen.DRAWS, [np.nextafter(1.0, 0.0)] * datagen.DRAWS])
+    X, labels, fam = datagen.from_uniforms(u)
+    assert fam.tolist() == [1, 9] and np.isfinite(X).all()
