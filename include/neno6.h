@@ -52,7 +52,7 @@ extern "C" {
 #define NENO6_STATUS_NONPHYSICAL_CELL 1 /* rho <= 0 or p <= 0 (or NaN)   */
 #define NENO6_STATUS_NONPHYSICAL_ROE 2  /* Roe-averaged c^2 <= 0         */
 #define NENO6_STATUS_TIMEOUT 4          /* a tensor-core wait gave up    */
-#define NENO6_STATUS_BAD_SAMPLE 8       /* mlp_train: index out of range */
+#define NENO6_STATUS_BAD_SAMPLE 8       /* mlp_train: index out of range; datagen: draw outside [0, 1) */
 
 /* neno6_config.precision */
 #define NENO6_FP64 0        /* everything in binary64 (bit-exact masks)    */
@@ -283,6 +283,30 @@ int neno6_mlp_train(neno6_handle* h, const double* X, const uint8_t* labels, int
  * handle.  Errors: ARG, CUDA.
  */
 int neno6_pipe_peak(int which, double* flops_per_s, void* stream);
+
+/*
+ * neno6_datagen — training samples of the classifier (Algorithm 1, Table 9,
+ * Sec. 3.2) generated on the device from caller-given uniform draws, one
+ * sample per row of u:
+ *   column 0  grid N in {50, 100, 200} (40 / 40 / 20 %) on [-1, 1];
+ *   column 1  function family 1..9 of Table 9, equally likely;
+ *   column 2  the interface x_{i+1/2}, i uniform in 2..N-4;
+ *   3..7      the family's parameters over Table 9's ranges;
+ *   column 8  sign (the sample is negated when u < 1/2).
+ * Labels: families 1-3 smooth (0); 4-8 eta_k = 1 iff a kink or jump lies
+ * strictly between the outermost cell centres of S_k; family 9 by the
+ * TENO6-opt selection (Eqs. (measureTENO)-(cut-off)).  Values are normalised
+ * by Eq. (normalizainput), as neno6_mlp_train and neno6_classify expect.
+ *   u       [n][NENO6_DATAGEN_DRAWS] float64 device array, values in [0, 1).
+ *   X       [n][6] float64 device array (out).
+ *   labels  [n] uint8 device array (out): eta_k in bit k.
+ *   family  nullable [n] uint8 device array (out): 1..9.
+ * A row with a draw outside [0, 1) is written as zeros (family 0) and sets
+ * NENO6_STATUS_BAD_SAMPLE.  Errors: ARG, SHAPE, ALIGN, CUDA.
+ */
+#define NENO6_DATAGEN_DRAWS 9
+int neno6_datagen(neno6_handle* h, const double* u, int64_t n, double* X, uint8_t* labels, uint8_t* family,
+                  void* stream);
 
 /*
  * neno6_status — synchronise `stream`, return the latched device status bits

@@ -21,6 +21,7 @@ ERRORS = {-1: "ARG", -2: "SHAPE", -3: "ALIGN", -4: "WEIGHTS", -5: "CUDA", -6: "N
 PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}
 BC = {"periodic": 0, "transmissive": 1}
 LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
+DATAGEN_DRAWS = 9  # uniform draws per training sample (neno6_datagen)
 MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
 LAW = {"advection": 0, "burgers": 1}
 # logit band re-evaluated in FP32 by the mixed-precision path
@@ -30,7 +31,7 @@ DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.5}
 EXPORTS = ("neno6_create", "neno6_destroy", "neno6_mask_bytes", "neno6_rhs", "neno6_step",
            "neno6_step_host", "neno6_classify", "neno6_status", "neno6_last_error", "neno6_step_noalloc",
            "neno6_rhs_vjp", "neno6_mlp_bwd", "neno6_guard_count", "neno6_mlp_train",
-           "neno6_scalar_rhs", "neno6_scalar_solve", "neno6_pipe_peak")
+           "neno6_scalar_rhs", "neno6_scalar_solve", "neno6_pipe_peak", "neno6_datagen")
 
 
 class Neno6Error(RuntimeError):
@@ -80,6 +81,7 @@ def load_library(path=LIB_PATH):
     lib.neno6_scalar_solve.argtypes = [vp, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int64), vp]
     lib.neno6_pipe_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.neno6_datagen.argtypes = [vp, dp, i64, dp, u8p, u8p, vp]
     lib.neno6_guard_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, vp]
     lib.neno6_step_noalloc.argtypes = [ctypes.POINTER(_Config), dp, i64, dp, ctypes.c_double,
                                        ctypes.c_double, dp, dp, vp, vp]
@@ -285,6 +287,20 @@ class Neno6:
                                               _ptr(adam_v), int(adam_t0), float(lr), _ptr(loss_sum),
                                               _stream()))
         return loss_sum
+
+    def datagen(self, u):
+        """Training samples of Table 9 from uniform draws u (float64 CUDA
+        tensor [n, 9], values in [0, 1)): returns (X [n, 6] float64,
+        labels [n] uint8, family [n] uint8), all on the device."""
+        assert u.is_cuda and u.dtype == torch.float64 and u.dim() == 2 and u.shape[1] == DATAGEN_DRAWS
+        u = u.contiguous()
+        n = u.shape[0]
+        X = torch.empty((n, 6), dtype=torch.float64, device=u.device)
+        labels = torch.empty(n, dtype=torch.uint8, device=u.device)
+        fam = torch.empty(n, dtype=torch.uint8, device=u.device)
+        self._check(self._lib.neno6_datagen(self._h, _ptr(u), n, _ptr(X), _ptr(labels), _ptr(fam),
+                                            _stream()))
+        return X, labels, fam
 
     def guard_count(self, reset=False):
         """Synchronise the current stream and return how many classifier rows

@@ -33,6 +33,7 @@ SOURCES = {
     "mlp_bwd.cu": [],
     "mlp_train.cu": [],
     "scalar.cu": ["-fmad=false"],
+    "datagen.cu": ["-fmad=false"],
     "peak.cu": [],
 }
 

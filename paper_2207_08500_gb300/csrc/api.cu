@@ -464,6 +464,18 @@ int neno6_step_host(neno6_handle* h, const double* U_in, double* U_out, double c
   return NENO6_OK;
 }
 
+int neno6_datagen(neno6_handle* h, const double* u, int64_t n, double* X, uint8_t* labels, uint8_t* family,
+                  void* stream) {
+  if (!h) return NENO6_ERR_ARG;
+  if (n < 0 || n >= (1ll << 40)) return fail(h, NENO6_ERR_SHAPE, "datagen: need 0 <= n < 2^40");
+  if (n == 0) return NENO6_OK;
+  if (!u || !X || !labels) return fail(h, NENO6_ERR_ARG, "datagen: null pointer");
+  if (!aligned(u, 8) || !aligned(X, 8)) return fail(h, NENO6_ERR_ALIGN, "datagen: misaligned");
+  cudaError_t e = launch_datagen(u, n, X, labels, family, h->d_status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "datagen launch");
+  return NENO6_OK;
+}
+
 int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out, double* logits,
                    void* stream) {
   if (!h) return NENO6_ERR_ARG;

@@ -167,6 +167,9 @@ struct MlpTrainArgs {
   int* status;
 };
 cudaError_t launch_mlp_train(const MlpTrainArgs& a, cudaStream_t s);
+// Training data of Table 9 from uniform draws u [n][9] (csrc/datagen.cu).
+cudaError_t launch_datagen(const double* u, long long n, double* X, uint8_t* labels, uint8_t* family,
+                           int* status, cudaStream_t s);
 cudaError_t launch_cfl_reduce(int ndim, const double* U, int nx, int ny, double gamma,
                               unsigned long long* smax, int* status, cudaStream_t s);
 
