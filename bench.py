@@ -311,6 +311,24 @@ def run_ours(args, rank, world):
                                     "mean_batch_loss": round(ls.item() / steps_ep, 5)}
         g64.close()
         del Uv, lam, gv, maskv, Xs, ys
+        # width study: neno6_classify throughput of the paper's network and
+        # of the 6-32-32-32-4 network on 2^22 stencils (FP64 and fp16)
+        Xw = torch.from_numpy(synth.mlp_stencils(1 << 22, seed=18)).to(dev)
+        narrow_w = os.path.join(os.path.dirname(neno6.DEFAULT_WEIGHTS), "neno6_mlp_6x32x32x32x4.bin")
+        wst = {}
+        for label, wpath in (("6-64-32-16-8-4", neno6.DEFAULT_WEIGHTS), ("6-32-32-32-4", narrow_w)):
+            for wprec in ("fp64", "fp16"):
+                gw = neno6.Neno6(ndim=1, nx=8, precision=wprec, weights=wpath)
+                gw.classify(Xw[:4096])
+                e_a.record(stream)
+                for _ in range(3):
+                    gw.classify(Xw)
+                e_b.record(stream)
+                torch.cuda.synchronize()
+                wst[label + " " + wprec] = round(3 * Xw.shape[0] / e_a.elapsed_time(e_b) / 1e6, 2)
+                gw.close()
+        extra["classify_Gstencils_per_s"] = wst
+        del Xw
 
     ms, e2e_ms, rhs_avg = max_over_ranks([ms, e2e_ms, rhs_avg], world, dev)
 

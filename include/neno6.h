@@ -21,7 +21,8 @@
  *    inside the library (periodic wrap or zero-gradient copy per axis).
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  All work is enqueued on it; no call synchronises the host
- *    except neno6_status and neno6_create/destroy.
+ *    except neno6_status, neno6_guard_count, neno6_step_host (whose state
+ *    lives in host memory) and neno6_create/destroy.
  *  - Every call returns NENO6_OK (0) or a negative NENO6_ERR_* code and
  *    never throws or aborts; neno6_last_error gives a one-line message.
  *    Conditions found on the device (a non-physical state) are latched in a
@@ -97,7 +98,10 @@ typedef struct neno6_handle neno6_handle;
  *                 count L, int32 widths[L+1], per layer W[out][in] then
  *                 b[out] as float64 little-endian, uint64 FNV-1a hash of the
  *                 payload).  The parameters (w^l, b^l) of Sec. 3.1,
- *                 Eq. (reconstuction).  Widths must be 6-64-32-16-8-4.
+ *                 Eq. (reconstuction).  Widths must be 6-64-32-16-8-4,
+ *                 or 6-32-32-32-4 (the width study's network): a handle
+ *                 holding the latter serves neno6_classify only, and every
+ *                 other call on it returns UNSUPPORTED.
  *   out           receives the handle (host pointer).
  * Allocates device memory for the weights and the status word; the RK3
  * stage buffers are allocated on the first neno6_step.

@@ -18,6 +18,7 @@ struct neno6_handle {
   neno6_config cfg;
   int nv = 0;
   int device = 0;
+  bool narrow = false;        // the 6-32-32-32-4 network (neno6_classify only)
   NetF64 net;                 // host copy of the classifier parameters
   double d[4];                // linear weights
   double cand[4][4];          // candidate coefficients
@@ -92,7 +93,7 @@ double rd_f64(const unsigned char* p) {
   return d;
 }
 
-int load_weights(const char* path, NetF64& net, std::string& msg) {
+int load_weights(const char* path, NetF64& net, bool& narrow, std::string& msg) {
   FILE* f = std::fopen(path, "rb");
   if (!f) {
     msg = std::string("cannot open weights file ") + path;
@@ -103,29 +104,29 @@ int load_weights(const char* path, NetF64& net, std::string& msg) {
   size_t n;
   while ((n = std::fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
   std::fclose(f);
-  const size_t nparams = kNetParams;
-  const size_t expect = 8 + 4 + 4 * 6 + 8 * nparams + 8;
   if (buf.size() < 16 || std::memcmp(buf.data(), "NENO6W01", 8) != 0) {
     msg = "weights file: bad magic";
     return NENO6_ERR_WEIGHTS;
   }
+  // the paper's 6-64-32-16-8-4 network, or the width study's 6-32-32-32-4
   const int32_t nl = rd_i32(&buf[8]);
-  if (nl != 5 || buf.size() != expect) {
-    msg = "weights file: only the 6-64-32-16-8-4 classifier is supported";
+  narrow = nl == 4;
+  const int* widths = narrow ? kNarrowWidths : kNetWidths;
+  const size_t nparams = narrow ? kNarrowParams : kNetParams;
+  const size_t expect = 8 + 4 + 4 * (size_t)(nl + 1) + 8 * nparams + 8;
+  bool ok = (nl == 5 || nl == 4) && buf.size() == expect;
+  for (int l = 0; ok && l <= nl; ++l) ok = rd_i32(&buf[12 + 4 * l]) == widths[l];
+  if (!ok) {
+    msg = "weights file: widths must be 6-64-32-16-8-4 (or 6-32-32-32-4 for neno6_classify)";
     return NENO6_ERR_WEIGHTS;
   }
-  for (int l = 0; l <= 5; ++l)
-    if (rd_i32(&buf[12 + 4 * l]) != kNetWidths[l]) {
-      msg = "weights file: widths are not 6-64-32-16-8-4";
-      return NENO6_ERR_WEIGHTS;
-    }
   const size_t payload = buf.size() - 16;
   if (fnv1a64(&buf[8], payload) != rd_u64(&buf[buf.size() - 8])) {
     msg = "weights file: checksum mismatch";
     return NENO6_ERR_WEIGHTS;
   }
-  const unsigned char* p = &buf[12 + 4 * 6];
-  for (size_t i = 0; i < nparams; ++i) net.p[i] = rd_f64(p + 8 * i);
+  const unsigned char* p = &buf[12 + 4 * (nl + 1)];
+  for (size_t i = 0; i < (size_t)kNetParams; ++i) net.p[i] = i < nparams ? rd_f64(p + 8 * i) : 0.0;
   return NENO6_OK;
 }
 
@@ -275,7 +276,7 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
   h->cfg = c;
   h->nv = c.ndim == 2 ? 4 : 3;
   std::string msg;
-  int rc = load_weights(weights_path, h->net, msg);
+  int rc = load_weights(weights_path, h->net, h->narrow, msg);
   if (rc != NENO6_OK) {
     delete h;
     return fail(nullptr, rc, msg);
@@ -297,7 +298,10 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
   }
   if (e == cudaSuccess && c.precision != NENO6_FP64) {
     std::vector<uint8_t> img(kNetImageBytes);
-    build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
+    if (h->narrow)
+      build_net_image_narrow(h->net, c.precision == NENO6_MIXED_BF16, img.data());
+    else
+      build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
     e = cudaMalloc(&h->d_net_image, kNetImageBytes);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_net_image, img.data(), kNetImageBytes, cudaMemcpyHostToDevice);
     std::vector<float> gimg(kNetParams);
@@ -351,6 +355,7 @@ int64_t neno6_mask_bytes(const neno6_handle* h) {
 int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mask_in,
               uint8_t* mask_out, void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs: the 6-32-32-32-4 network serves neno6_classify only");
   if (!U || !dUdt) return fail(h, NENO6_ERR_ARG, "rhs: null state pointer");
   if (h->cfg.precision != NENO6_FP64) {
     if (mask_in) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs: frozen masks need the FP64 path");
@@ -377,6 +382,7 @@ int neno6_rhs(neno6_handle* h, const double* U, double* dUdt, const uint8_t* mas
 int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_dev, double* dt_dev,
                void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "step: the 6-32-32-32-4 network serves neno6_classify only");
   if (!U) return fail(h, NENO6_ERR_ARG, "step: null state pointer");
 
   if (!aligned(U, 16)) return fail(h, NENO6_ERR_ALIGN, "step: U must be 16-byte aligned");
@@ -434,6 +440,7 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
 int neno6_step_host(neno6_handle* h, const double* U_in, double* U_out, double cfl, double t_end,
                     double* t_io, void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "step_host: the 6-32-32-32-4 network serves neno6_classify only");
   if (!U_in || !U_out) return fail(h, NENO6_ERR_ARG, "step_host: null state pointer");
   if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step_host: need cfl > 0, t_end >= 0");
   cudaStream_t s = (cudaStream_t)stream;
@@ -485,7 +492,8 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
   if (!aligned(X, 8) || (logits && !aligned(logits, 8))) return fail(h, NENO6_ERR_ALIGN, "classify: misaligned");
   if (h->cfg.precision != NENO6_FP64) {
     cudaError_t e = launch_classify_mixed(X, n, eta_out, logits, h->d_net_image,
-                                          h->cfg.precision == NENO6_MIXED_BF16, h->d_status, (cudaStream_t)stream);
+                                          h->cfg.precision == NENO6_MIXED_BF16, h->narrow, h->d_status,
+                                          (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "classify launch");
     return NENO6_OK;
   }
@@ -495,7 +503,7 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
   p.logits = logits;
   p.n = n;
   p.net = h->net;
-  cudaError_t e = launch_classify_fp64(p, (cudaStream_t)stream);
+  cudaError_t e = launch_classify_fp64(p, h->narrow, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "classify launch");
   return NENO6_OK;
 }
@@ -503,6 +511,7 @@ int neno6_classify(neno6_handle* h, const double* X, int64_t n, uint8_t* eta_out
 int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const uint8_t* mask,
                   double* grad_U, void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "rhs_vjp: the 6-32-32-32-4 network serves neno6_classify only");
   if (!U || !lambda || !grad_U) return fail(h, NENO6_ERR_ARG, "rhs_vjp: null pointer");
   if (!aligned(U, 16) || !aligned(lambda, 16) || !aligned(grad_U, 16))
     return fail(h, NENO6_ERR_ALIGN, "rhs_vjp: arrays must be 16-byte aligned");
@@ -544,6 +553,7 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
 int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64_t n, float* grad, float* loss,
                   void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "mlp_bwd: the 6-32-32-32-4 network serves neno6_classify only");
   if (n < 1 || n >= (1ll << 31)) return fail(h, NENO6_ERR_SHAPE, "mlp_bwd: need 1 <= n < 2^31");
   if (!X || !labels || !grad) return fail(h, NENO6_ERR_ARG, "mlp_bwd: null pointer");
   if (!aligned(X, 8) || !aligned(grad, 4) || (loss && !aligned(loss, 4)))
@@ -566,6 +576,8 @@ int scalar_check(neno6_handle* h, int law, const void* u, const char* who) {
   if (!h) return NENO6_ERR_ARG;
   if (h->cfg.ndim != 1 || h->cfg.precision != NENO6_FP64)
     return fail(h, NENO6_ERR_UNSUPPORTED, std::string(who) + ": needs a 1D FP64 handle");
+  if (h->narrow)
+    return fail(h, NENO6_ERR_UNSUPPORTED, std::string(who) + ": the 6-32-32-32-4 network serves neno6_classify only");
   if (law != NENO6_LAW_ADVECTION && law != NENO6_LAW_BURGERS)
     return fail(h, NENO6_ERR_ARG, std::string(who) + ": unknown law");
   if (!u) return fail(h, NENO6_ERR_ARG, std::string(who) + ": null pointer");
@@ -654,6 +666,7 @@ int neno6_mlp_train(neno6_handle* h, const double* X, const uint8_t* labels, int
                     int64_t n_perm, int batch, float* params, float* adam_m, float* adam_v, int64_t adam_t0,
                     double lr, double* loss_sum, void* stream) {
   if (!h) return NENO6_ERR_ARG;
+  if (h->narrow) return fail(h, NENO6_ERR_UNSUPPORTED, "mlp_train: the 6-32-32-32-4 network serves neno6_classify only");
   if (n < 1 || n >= (1ll << 31) || n_perm < 1 || n_perm >= (1ll << 31))
     return fail(h, NENO6_ERR_SHAPE, "mlp_train: need 1 <= n, n_perm < 2^31");
   if (batch < 1 || batch > kMaxTrainBatch) return fail(h, NENO6_ERR_SHAPE, "mlp_train: need 1 <= batch <= 192");

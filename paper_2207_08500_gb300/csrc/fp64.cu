@@ -396,6 +396,22 @@ __global__ void __launch_bounds__(256) classify_fp64_kernel(const __grid_constan
   }
 }
 
+// The same for the 6-32-32-32-4 network of the width study.
+__global__ void __launch_bounds__(256) classify_fp64_narrow_kernel(const __grid_constant__ ClassifyParamsF64 P) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.n) return;
+  double s[6], x[6], z[4];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) s[j] = P.X[r * 6 + j];
+  normalise6(s, x);
+  const unsigned eta = mlp64_narrow(P.net.p, x, z);
+  P.eta[r] = (uint8_t)eta;
+  if (P.logits) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) P.logits[r * 4 + k] = z[k];
+  }
+}
+
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
   return a > b ? a : b;
 }
@@ -470,10 +486,13 @@ cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s) {
+cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, bool narrow, cudaStream_t s) {
   if (p.n == 0) return cudaSuccess;
   const long long blocks = (p.n + 255) / 256;
-  classify_fp64_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+  if (narrow)
+    classify_fp64_narrow_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+  else
+    classify_fp64_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

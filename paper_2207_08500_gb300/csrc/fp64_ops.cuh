@@ -79,6 +79,46 @@ __device__ __forceinline__ unsigned mlp64(const double* __restrict__ W, const do
   return eta;
 }
 
+// The 6-32-32-32-4 classifier of the width study, same arithmetic order
+// (bias, then an fma chain over the inputs in ascending order; ReLU on hidden
+// layers); layers 1+2 and 3+4 fused as in mlp64.  Packed offsets: W1 0 /
+// b1 192, W2 224 / b2 1248, W3 1280 / b3 2304, W4 2336 / b4 2464.
+__device__ __forceinline__ unsigned mlp64_narrow(const double* __restrict__ W, const double* x, double* z) {
+  double a2[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) a2[o] = W[1248 + o];
+#pragma unroll 4
+  for (int i = 0; i < 32; ++i) {
+    double h = W[192 + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h = __fma_rn(W[i * 6 + k], x[k], h);
+    h = relu(h);
+#pragma unroll
+    for (int o = 0; o < 32; ++o) a2[o] = __fma_rn(W[224 + o * 32 + i], h, a2[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 32; ++o) a2[o] = relu(a2[o]);
+  double a4[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) a4[o] = W[2464 + o];
+#pragma unroll 4
+  for (int j = 0; j < 32; ++j) {
+    double h = W[2304 + j];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) h = __fma_rn(W[1280 + j * 32 + i], a2[i], h);
+    h = relu(h);
+#pragma unroll
+    for (int o = 0; o < 4; ++o) a4[o] = __fma_rn(W[2336 + o * 32 + j], h, a4[o]);
+  }
+  unsigned eta = 0;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    z[o] = a4[o];
+    eta |= (gt0(a4[o]) ? 1u : 0u) << o;
+  }
+  return eta;
+}
+
 // Eq. (normalizainput): divide by max(|s_0|, ..., |s_5|, 1).  s/1 == s
 // exactly, so the division is skipped when the maximum is 1.
 __device__ __forceinline__ void normalise6(const double* s, double* x) {

@@ -78,6 +78,25 @@ constexpr int kNetImageBytes = kNetImageW5 + 4 * 8 * 4;
 static_assert(kNetImageBytes % 16 == 0, "image is copied in 16-byte chunks");
 
 void build_net_image(const NetF64& net, bool bf16, uint8_t* img);
+
+// The 6-32-32-32-4 network of the width study (neno6_classify only): its
+// 2468 parameters occupy the start of NetF64 in the same packed order.  Its
+// tensor-core image, in the same kNetImageBytes buffer: B1 32 x 16 (b1's
+// terms in the ones columns), B2 32 x 32, B2b 32 x 16 (b2's terms), B3
+// 32 x 32, then the FP32 b3[32], W4^T[32][4] and b4[4] (layer 4 on the CUDA
+// cores).
+constexpr int kNarrowWidths[5] = {6, 32, 32, 32, 4};
+constexpr int kNarrowParams = 6 * 32 + 32 + 32 * 32 + 32 + 32 * 32 + 32 + 32 * 4 + 4;
+static_assert(kNarrowParams == 2468 && kNarrowParams <= kNetParams, "6-32-32-32-4 parameter count");
+constexpr int kNarrowB1 = 0;                          // 32 x 16
+constexpr int kNarrowB2 = kNarrowB1 + 32 * 16 * 2;    // 32 x 32
+constexpr int kNarrowB2b = kNarrowB2 + 32 * 32 * 2;   // 32 x 16
+constexpr int kNarrowB3 = kNarrowB2b + 32 * 16 * 2;   // 32 x 32
+constexpr int kNarrowBias3 = kNarrowB3 + 32 * 32 * 2;  // 32 floats
+constexpr int kNarrowW4 = kNarrowBias3 + 32 * 4;       // 32 x 4 floats, then b4[4]
+constexpr int kNarrowBytes = kNarrowW4 + 32 * 4 * 4 + 4 * 4;
+static_assert(kNarrowBytes <= kNetImageBytes && kNarrowBytes % 16 == 0, "narrow image fits the buffer");
+void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img);
 // FP32 parameters with every W transposed to [in][out] (guard re-evaluation).
 void build_guard_image(const NetF64& net, float* img);
 
@@ -125,8 +144,9 @@ cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, doubl
 
 cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
-                                  const uint8_t* net_image, bool bf16, int* status, cudaStream_t s);
-cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, cudaStream_t s);
+                                  const uint8_t* net_image, bool bf16, bool narrow, int* status,
+                                  cudaStream_t s);
+cudaError_t launch_classify_fp64(const ClassifyParamsF64& p, bool narrow, cudaStream_t s);
 // scratch: vjp_scratch_bytes(ndim, nx, ny) bytes (per-face contributions)
 size_t vjp_scratch_bytes(int ndim, int nx, int ny);
 cudaError_t launch_rhs_vjp(int ndim, const RhsArgs& a, const double* lam, double* grad, double* scratch,

@@ -40,7 +40,7 @@ using namespace tcmlp;
 // their 64-column TMEM allocations always fit in the 512 columns.
 constexpr int kResidencyPad = 16 * 1024;
 
-template <bool BF16>
+template <bool BF16, bool NARROW>
 __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const double* __restrict__ X,
                                                                       long long n, uint8_t* __restrict__ eta,
                                                                       double* __restrict__ logits,
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const doubl
     fence_async_smem();
     __syncthreads();
     float z[4];
-    if (!mlp_tc<BF16>(c, z)) {
+    if (!(NARROW ? mlp_tc_narrow<BF16>(c, z) : mlp_tc<BF16>(c, z))) {
       if (t == 0) atomicOr(status, 4);
       break;
     }
@@ -178,8 +178,48 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
   }
 }
 
+// Host: the tensor-core image of the 6-32-32-32-4 network (kNarrow* layout).
+void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
+  std::memset(img, 0, kNetImageBytes);
+  auto bits = [&](double w) { return bf16 ? to_bf16_bits(w) : to_fp16_bits(w); };
+  auto put_bits = [&](int off, int K, int n, int k, uint16_t b) {
+    std::memcpy(img + off + kmajor_offset(n, k, K), &b, 2);
+  };
+  auto put_bias = [&](int off, int n, double b) {
+    for (int q = 0; q < 3; ++q) {
+      const uint16_t h = bits(b);
+      put_bits(off, 16, n, kOnesCol + q, h);
+      b -= from_16_bits(h, bf16);
+    }
+  };
+  const int boff[3] = {kNarrowB1, kNarrowB2, kNarrowB3};
+  const int Kpad[3] = {16, 32, 32};
+  float* b3 = reinterpret_cast<float*>(img + kNarrowBias3);
+  float* w4t = reinterpret_cast<float*>(img + kNarrowW4);
+  size_t p = 0;
+  for (int l = 0; l < 4; ++l) {
+    const int nin = kNarrowWidths[l], nout = kNarrowWidths[l + 1];
+    for (int o = 0; o < nout; ++o)
+      for (int i = 0; i < nin; ++i) {
+        const double w = net.p[p + (size_t)o * nin + i];
+        if (l < 3) put_bits(boff[l], Kpad[l], o, i, bits(w));
+        else w4t[i * 4 + o] = (float)w;
+      }
+    p += (size_t)nout * nin;
+    for (int o = 0; o < nout; ++o) {
+      const double b = net.p[p + o];
+      if (l == 0) put_bias(kNarrowB1, o, b);
+      else if (l == 1) put_bias(kNarrowB2b, o, b);
+      else if (l == 2) b3[o] = (float)b;
+      else w4t[128 + o] = (float)b;
+    }
+    p += nout;
+  }
+}
+
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
-                                  const uint8_t* net_image, bool bf16, int* status, cudaStream_t s) {
+                                  const uint8_t* net_image, bool bf16, bool narrow, int* status,
+                                  cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const long long tiles = (n + 127) / 128;
   // the static shared memory (~30 KB with the per-CTA reserve) caps
@@ -188,10 +228,20 @@ cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, do
                 "nine resident CTAs would oversubscribe TMEM");
   static_assert(kNetImageBytes + kBufYBytes + kResidencyPad <= 48 * 1024, "no opt-in needed");
   const int blocks = (int)(tiles < 152 * 6 ? tiles : 152 * 6);
-  if (bf16)
-    classify_mixed_kernel<true><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image, status);
-  else
-    classify_mixed_kernel<false><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image, status);
+  if (narrow) {
+    if (bf16)
+      classify_mixed_kernel<true, true><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image,
+                                                                                  status);
+    else
+      classify_mixed_kernel<false, true><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image,
+                                                                                   status);
+  } else if (bf16) {
+    classify_mixed_kernel<true, false><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image,
+                                                                                 status);
+  } else {
+    classify_mixed_kernel<false, false><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image,
+                                                                                  status);
+  }
   return cudaGetLastError();
 }
 

@@ -228,6 +228,42 @@ __device__ __forceinline__ bool mlp_tc(MlpCtx& c, float z[4]) {
   return __syncthreads_or(*c.fail) == 0;
 }
 
+// The 6-32-32-32-4 network of the width study (neno6_classify only), image
+// layout kNarrow*: layers 1-3 on the tensor cores (N = 32), every
+// accumulator in TMEM columns [0,32) and every 16-bit operand of layers 2-3
+// in [32,48); b1 and b2 ride on the ones columns as above, b3 is added in
+// FP32 and layer 4 (32 -> 4) runs in FP32 on the CUDA cores on the FP32
+// ReLU output of layer 3 (bias, then an FMA per input in ascending order).
+template <bool BF16>
+__device__ __forceinline__ bool mlp_tc_narrow(MlpCtx& c, float z[4]) {
+  const int t = threadIdx.x;
+  if (t == 0) issue_layer<BF16>(c, c.bufY, 16, kNarrowB1, 32, 0);
+  wait_layer(c);
+  hidden_epilogue<32, BF16>(c, 0, 32);
+  if (t == 0) issue_layer_t<BF16>(c, 32, 32, kNarrowB2, 32, 0, kNarrowB2b);
+  wait_layer(c);
+  hidden_epilogue<32, BF16>(c, 0, 32);
+  if (t == 0) issue_layer_t<BF16>(c, 32, 32, kNarrowB3, 32, 0);
+  wait_layer(c);
+  const uint32_t lane = (uint32_t)(t & ~31) << 16;
+  uint32_t r[16], q[16];
+  tmem_ld16(c.tmem + lane, r);
+  tmem_ld16(c.tmem + lane + 16u, q);
+  tmem_ld_wait();
+  tc_fence_before();
+  const float* b3 = reinterpret_cast<const float*>(c.net + kNarrowBias3);
+  const float* w4t = reinterpret_cast<const float*>(c.net + kNarrowW4);  // [32][4], then b4
+#pragma unroll
+  for (int k = 0; k < 4; ++k) z[k] = w4t[128 + k];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const float h = fmaxf(__uint_as_float(i < 16 ? r[i] : q[i - 16]) + b3[i], 0.0f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) z[k] = fmaf(w4t[i * 4 + k], h, z[k]);
+  }
+  return __syncthreads_or(*c.fail) == 0;
+}
+
 // Copy the classifier image (16-byte chunks) into shared memory.
 __device__ __forceinline__ void load_net_image(uint8_t* dst, const uint8_t* __restrict__ src) {
   const uint4* s = reinterpret_cast<const uint4*>(src);

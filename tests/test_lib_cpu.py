@@ -74,16 +74,18 @@ def test_solver_refuses_without_gpu():
 
 
 def test_create_rejects_other_network_widths(lib_path, tmp_path):
-    """The kernels are written for the 6-64-32-16-8-4 classifier of Sec. 3.1;
-    a weights file of another shape (here 6-32-32-32-4) is refused on the
-    host with NENO6_ERR_WEIGHTS, before any device work."""
+    """The kernels are written for the 6-64-32-16-8-4 classifier of Sec. 3.1
+    and, for neno6_classify, the width study's 6-32-32-32-4; a weights file of
+    any other shape (here 6-32-16-4, and 6-64-32-16-4) is refused on the host
+    with NENO6_ERR_WEIGHTS, before any device work."""
     import paper_2207_08500_gb300 as p
     from oracle.weights import Net
     lib = p.load_library(lib_path)
-    path = tmp_path / "w32.bin"
-    Net.random(widths=(6, 32, 32, 32, 4), seed=3).save(path)
     c = p._Config()
     c.ndim, c.nx, c.ny, c.dx, c.dy, c.gamma = 2, 8, 8, 0.1, 0.1, 1.4
-    h = ctypes.c_void_p()
-    assert lib.neno6_create(ctypes.byref(c), str(path).encode(), ctypes.byref(h)) == -4
-    assert b"6-64-32-16-8-4" in lib.neno6_last_error(None)
+    for widths in [(6, 32, 16, 4), (6, 64, 32, 16, 4), (6, 32, 32, 16, 4)]:
+        path = tmp_path / ("w%d.bin" % len(widths))
+        Net.random(widths=widths, seed=3).save(path)
+        h = ctypes.c_void_p()
+        assert lib.neno6_create(ctypes.byref(c), str(path).encode(), ctypes.byref(h)) == -4
+        assert b"6-64-32-16-8-4" in lib.neno6_last_error(None)
