@@ -170,7 +170,7 @@ void candidates(const OracleParams& P, const T s[6], T f[4]) {
 }
 
 // Eqs. (TENOweight_renormalize) and (convex), with the first-order fallback
-// of Algorithm 2 step 4 when every stencil is discarded.
+// of Algorithm 2 when every stencil is discarded.
 template <class T>
 T combine(const OracleParams& P, const T s[6], unsigned eta) {
   T f[4];

@@ -21,7 +21,7 @@ family 6 joins (x-a1)^k1 and (x-a2)^k2 (integer k in 2..8) continuously at a
 kink x_k ~ U[-0.6, 0.6]; family 8 places the jump at the sampled interface
 (data "only collected at x_{i+1/2} = x_0") for half of its samples and at
 another face inside the stencil for the other half, standing in for the
-temporally evolved discontinuous solutions of Algorithm 1 step 1, which are
+temporally evolved discontinuous solutions that Algorithm 1 collects, which are
 not generated; family 9 uses N_f ~ U[N/8, N/2].
 
 Sign reading.  Table 9 draws the levels of family 8 from U[0, 2], so every
@@ -109,7 +109,7 @@ def generate(n, seed=20220717):
     sing[m, 1] = (a + 1.0 / al)[m]
     # 8: step x_l / x_r; half with the jump at the interface x_{i+1/2}
     # (Table 9), half at another face inside the stencil (stand-in for the
-    # advected discontinuities of Algorithm 1 step 1)
+    # advected discontinuities Algorithm 1 collects)
     xl, xr = u(-2, 2), u(-2, 2)
     m = fam == 8
     shift = np.where(rng.uniform(size=n) < 0.5, 0, rng.integers(-2, 3, size=n))

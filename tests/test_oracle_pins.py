@@ -113,7 +113,7 @@ def test_combination_polynomial_exactness(oracle_mod, kind, deg):
 
 def test_renormalised_weights_and_fallback(oracle_mod):
     """Eq. (TENOweight_renormalize): the kept weights are d_k / sum of kept d;
-    Algorithm 2 step 4: all discarded -> the first-order upwind value s_2."""
+    Algorithm 2: all discarded -> the first-order upwind value s_2."""
     from oracle import coefficients
     o = oracle_mod.Oracle(ndim=1, nx=8)
     d = coefficients.linear_weights("paper")
