@@ -507,6 +507,28 @@ def run_rhs_only(args):
                       "launches": args.warmup + args.steps, "status": g.status()}))
 
 
+def run_classify_only(args):
+    """`--classify-only`: warm-up + `--steps` neno6_classify calls on `--n`
+    sine / step stencils with the paper's network, then the same with the
+    6-32-32-32-4 network of the width study (`--precision`), a case for
+    profilers; prints one line, no timing."""
+    import torch
+    import paper_2207_08500_gb300 as neno6
+    import synth
+    X = torch.from_numpy(synth.mlp_stencils(args.n, seed=18)).cuda()
+    narrow = os.path.join(os.path.dirname(neno6.DEFAULT_WEIGHTS), "neno6_mlp_6x32x32x32x4.bin")
+    status = []
+    for wpath in (neno6.DEFAULT_WEIGHTS, narrow):
+        g = neno6.Neno6(ndim=1, nx=8, precision=args.precision, weights=wpath)
+        for _ in range(args.warmup + args.steps):
+            g.classify(X)
+        torch.cuda.synchronize()
+        status.append(g.status())
+        g.close()
+    print(json.dumps({"classify_only": True, "n": args.n, "precision": args.precision,
+                      "launches_per_network": args.warmup + args.steps, "status": status}))
+
+
 def run_oblique(args):
     """`--workload oblique`: 8192 x 4096 transmissive oblique-shock state
     (square cells on [0, 2] x [0, 1]), mixed-precision steps replayed from a
@@ -585,6 +607,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--rhs-only", action="store_true")
     ap.add_argument("--vjp-only", action="store_true")
+    ap.add_argument("--classify-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--cpu-crop", type=int, default=384)
@@ -592,6 +615,10 @@ def main():
     args = ap.parse_args()
     if args.workload == "oblique" and args.impl == "ours":
         print(json.dumps(run_oblique(args)))
+        return
+    if args.classify_only:
+        args.n = args.n or (1 << 20)
+        run_classify_only(args)
         return
     if args.n is None:
         args.n = 2048 if args.precision == "fp64" else 4096
