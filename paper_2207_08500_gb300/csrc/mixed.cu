@@ -35,10 +35,14 @@ using namespace tcmlp;
 // Batched classifier (neno6_classify, mixed precision): persistent CTAs of
 // 128 threads, one 128-row tile per iteration.  Normalisation (Eq.
 // (normalizainput)) in FP32, then the tensor-core MLP; logit > 0 -> discard.
-// Dynamic shared memory requested at launch and never touched: it keeps a
-// CTA's shared memory at ~30 KB, so that at most seven are resident per SM and
-// their 64-column TMEM allocations always fit in the 512 columns.
-constexpr int kResidencyPad = 16 * 1024;
+// Dynamic shared memory requested at launch and never touched: it brings a
+// CTA's shared memory to ~28 KB, so that eight are resident per SM (their
+// 8 x 64 TMEM columns are exactly the SM's 512) and a ninth never is, whose
+// allocation would wait.
+constexpr int kResidencyPad = 14 * 1024;
+// static shared memory of the kernel below: image, input tile, barrier, TMEM
+// address, timeout flag
+constexpr int kClassifySmem = kNetImageBytes + kBufYBytes + 16;
 
 template <bool BF16, bool NARROW>
 __global__ void __launch_bounds__(kMlpThreads) classify_mixed_kernel(const double* __restrict__ X,
@@ -222,12 +226,13 @@ cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, do
                                   cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const long long tiles = (n + 127) / 128;
-  // the static shared memory (~30 KB with the per-CTA reserve) caps
-  // residency at seven CTAs of the SM's 228 KB (see s_residency_pad)
-  static_assert(kNetImageBytes + kBufYBytes + kResidencyPad + 1024 > 228 * 1024 / 9,
-                "nine resident CTAs would oversubscribe TMEM");
-  static_assert(kNetImageBytes + kBufYBytes + kResidencyPad <= 48 * 1024, "no opt-in needed");
-  const int blocks = (int)(tiles < 152 * 6 ? tiles : 152 * 6);
+  // shared memory per CTA (128-byte units plus the 1 KB per-CTA reserve)
+  // admits eight CTAs to the SM's 228 KB and never nine (kResidencyPad)
+  constexpr int kPerCta = (kClassifySmem + kResidencyPad + 127) / 128 * 128 + 1024;
+  static_assert(8 * kPerCta <= 228 * 1024, "eight resident CTAs");
+  static_assert(9 * kPerCta > 228 * 1024, "nine resident CTAs would oversubscribe TMEM");
+  static_assert(kClassifySmem + kResidencyPad <= 48 * 1024, "no opt-in needed");
+  const int blocks = (int)(tiles < 152 * 8 ? tiles : 152 * 8);
   if (narrow) {
     if (bf16)
       classify_mixed_kernel<true, true><<<blocks, kMlpThreads, kResidencyPad, s>>>(X, n, eta, logits, net_image,
