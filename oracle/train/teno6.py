@@ -72,16 +72,26 @@ def smoothness(F):
     return np.maximum(b, 0.0), np.maximum(b6, 0.0)
 
 
-def select(F):
-    """TENO6-opt delta_k (1 = smooth, kept) for stencils F [n, 6]."""
+def tau6(b, b6):
+    """Eq. (taukTENO): tau_6 = |beta_6 - (beta_1 + beta_2 + 4 beta_0) / 6|."""
+    return np.abs(b6 - (b[:, 1] + b[:, 2] + 4.0 * b[:, 0]) / 6.0)
+
+
+def chi(F):
+    """chi_k of Eq. (normalize) for stencils F [n, 6]: gamma_k of Eq.
+    (measureTENO) normalised to sum 1 (in the log domain, a stable softmax)."""
     b, b6 = smoothness(F)
-    tau = np.abs(b6 - (b[:, 1] + b[:, 2] + 4.0 * b[:, 0]) / 6.0)
-    # log gamma_k = q log(C + tau / (beta_k + eps)); chi via a stable softmax
+    tau = tau6(b, b6)
     lg = Q * np.log(C + tau[:, None] / (b + EPS))
     lg -= lg.max(axis=1, keepdims=True)
     g = np.exp(lg)
-    chi = g / g.sum(axis=1, keepdims=True)
-    return (chi >= CT).astype(np.uint8)
+    return g / g.sum(axis=1, keepdims=True)
+
+
+def select(F):
+    """TENO6-opt delta_k (1 = smooth, kept) for stencils F [n, 6]: the
+    cut-off of Eq. (cut-off)."""
+    return (chi(F) >= CT).astype(np.uint8)
 
 
 def labels(F):

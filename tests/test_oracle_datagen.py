@@ -125,6 +125,15 @@ def test_from_uniforms_same_distribution_as_generate():
         assert np.abs(a - b).max() < 0.03, (f, a, b)
 
 
+def test_from_uniforms_sign_rule():
+    """The reading of Table 9's signs: a sample is negated iff its sign draw
+    is below 1/2 (family 3, a positive Gaussian, shows the sign)."""
+    u, X, eta, fam = _from_uniforms(6000, seed=15)
+    m = fam == 3
+    assert ((X[m] < 0).all(axis=1) == (u[m, 8] < 0.5)).all()
+    assert ((X[m] > 0).all(axis=1) == (u[m, 8] >= 0.5)).all()
+
+
 def test_from_uniforms_edges_of_the_draws():
     # the smallest and largest draws map inside every range
     u = np.array([[0.0] * datagen.DRAWS, [np.nextafter(1.0, 0.0)] * datagen.DRAWS])

@@ -75,15 +75,36 @@ def test_indicator_invariants():
 
 
 def test_tau6_is_sixth_order():
-    """tau_6 = O(dx^6) on smooth data: halving dx divides it by ~2^6."""
+    """tau_6 = O(dx^6) on smooth data (Eq. (taukTENO)): halving dx divides it
+    by ~2^6, while the indicators themselves are O(dx^2)."""
     j = np.arange(-2, 4)
-    taus = []
+    taus, b0 = [], []
     for h in (0.1, 0.05, 0.025):
         F = (np.cos(1.3 * (j + 0.5) * h) - np.cos(1.3 * (j - 0.5) * h)) / (1.3 * h) * -1
         b, b6 = teno6.smoothness(F[None, :])
-        taus.append(abs(b6[0] - (b[0, 1] + b[0, 2] + 4 * b[0, 0]) / 6))
+        taus.append(teno6.tau6(b, b6)[0])
+        b0.append(b[0, 0])
     orders = np.log2(np.array(taus[:-1]) / np.array(taus[1:]))
     assert np.all(orders > 5.7), orders
+    assert np.all(np.abs(np.log2(np.array(b0[:-1]) / np.array(b0[1:])) - 2) < 0.1)
+
+
+def test_cut_off_constants_and_chi():
+    """Eq. (measureTENO) and (cut-off) with the printed C = 1, q = 6,
+    eps = 1e-40, C_T = 1e-6: chi sums to 1, does not depend on the scale of
+    the data, and the selection is exactly chi >= 1e-6."""
+    assert (teno6.C, teno6.Q, teno6.EPS, teno6.CT) == (1.0, 6, 1e-40, 1e-6)
+    rng = np.random.default_rng(5)
+    j = np.arange(-2, 4)
+    # sines near the grid frequency, some with a jump: chi spans many decades
+    F = np.sin(rng.uniform(0.2, 2.8, (20000, 1)) * j + rng.uniform(0, 6.3, (20000, 1)))
+    F[::3] += rng.uniform(-1, 1, (len(F[::3]), 1)) * (j >= rng.integers(-1, 4, (len(F[::3]), 1)))
+    c = teno6.chi(F)
+    np.testing.assert_allclose(c.sum(axis=1), 1.0, rtol=1e-12)
+    np.testing.assert_allclose(teno6.chi(7.5 * F), c, rtol=1e-9, atol=1e-300)
+    assert np.array_equal(teno6.select(F), (c >= 1e-6).astype(np.uint8))
+    near = (c > 1e-7) & (c < 1e-5)
+    assert near.sum() > 20  # the threshold is exercised on both sides
 
 
 def test_selection_on_smooth_data_and_jumps():
@@ -102,3 +123,18 @@ def test_selection_on_smooth_data_and_jumps():
     b, b6 = teno6.smoothness(np.array([[0, 1, 1, 1, 1, 1.0], [2, 2, 2, 2, 2, 2.0]]))
     assert (b >= 0).all() and (b6 >= 0).all()
     assert teno6.select(np.array([[2, 2, 2, 2, 2, 2.0]])).tolist() == [[1, 1, 1, 1]]
+
+
+def test_chi_exponent_is_q(monkeypatch):
+    """gamma_k is a q-th power (Eq. (measureTENO)): the log ratio of two
+    stencils' chi is proportional to q, and q is the printed 6."""
+    rng = np.random.default_rng(6)
+    j = np.arange(-2, 4)
+    F = np.sin(rng.uniform(0.5, 2.5, (200, 1)) * j + rng.uniform(0, 6.3, (200, 1)))
+    c6 = teno6.chi(F)
+    monkeypatch.setattr(teno6, "Q", 3)
+    c3 = teno6.chi(F)
+    l6 = np.log(c6[:, 0] / c6[:, 1])
+    l3 = np.log(c3[:, 0] / c3[:, 1])
+    ok = np.abs(l3) > 1e-3
+    np.testing.assert_allclose(l6[ok], 2.0 * l3[ok], rtol=1e-9)
