@@ -100,8 +100,12 @@ typedef struct neno6_handle neno6_handle;
  *                 payload).  The parameters (w^l, b^l) of Sec. 3.1,
  *                 Eq. (reconstuction).  Widths must be 6-64-32-16-8-4,
  *                 or 6-32-32-32-4 (the width study's network): a handle
- *                 holding the latter serves neno6_classify only, and every
- *                 other call on it returns UNSUPPORTED.
+ *                 holding the latter serves neno6_classify (and the calls
+ *                 that use no network: neno6_datagen, neno6_status,
+ *                 neno6_guard_count, neno6_mask_bytes, neno6_last_error,
+ *                 neno6_destroy); the right-hand-side, step, adjoint,
+ *                 backward, training and scalar-law calls return UNSUPPORTED
+ *                 on it.
  *   out           receives the handle (host pointer).
  * Allocates device memory for the weights and the status word; the RK3
  * stage buffers are allocated on the first neno6_step.
