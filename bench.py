@@ -386,7 +386,7 @@ def run_ours(args, rank, world):
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernels at 2048^2 (profiles/*.md), scaled by cells
+# capture of the current kernels at 2048^2, scaled by cells
 # for other grids (the traffic is U once, the face fluxes once and the halo
 # re-reads, all proportional to the cells)
 TRAFFIC_2048 = {True: 141.2e6 + 96.6e6, False: 287.6e6 + 236.8e6}

@@ -364,7 +364,11 @@ const char* neno6_last_error(const neno6_handle* h);
  * overlaps on the GPU (different streams, or different host threads) race on
  * it and must be serialised by the caller.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.
+ * current); make that first call before any stream capture.  The address is
+ * kept per device together with the id of the context it was taken in; after
+ * a device reset (or a release of the primary context) the next call sees a
+ * new context id and looks the address up again, so that call too should
+ * come before any stream capture.
  *
  *   cfg          host pointer: grid and scheme (precision must be NENO6_FP64);
  *                nv * nx * ny must not exceed NENO6_NOALLOC_MAX_STATE_ELEMS.

@@ -46,6 +46,40 @@ struct neno6_handle {
   std::string err;
 };
 
+namespace neno6 {
+
+void scheme_tables(int linear_weights, double d[4], double cand[4][4], double wtab[16][4]) {
+  if (linear_weights == NENO6_W_SIXTH) {
+    d[0] = 9.0 / 20.0;
+    d[1] = 3.0 / 10.0;
+    d[2] = 1.0 / 20.0;
+    d[3] = 1.0 / 5.0;
+  } else {  // Sec. 2.2 / Sec. 4 (TENO6-opt optimal weights)
+    d[0] = 0.4294317718960898;
+    d[1] = 0.1727270875843552;
+    d[2] = 0.0855682281039113;
+    d[3] = 0.312272912415645;
+  }
+  // Reconstruction of h(x_{i+1/2}) from point values acting as cell averages
+  // (Eqs. (definitionEq), (approximatepolynomial)) on S0 = {i-1,i,i+1},
+  // S1 = {i,i+1,i+2}, S2 = {i-2,i-1,i}, S3 = {i,i+1,i+2,i+3}.
+  const double c[4][4] = {{-1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
+                          {1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
+                          {1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0},
+                          {1.0 / 4.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0}};
+  std::memcpy(cand, c, sizeof c);
+  // Eq. (TENOweight_renormalize): w_k = d_k delta_k / sum_k d_k delta_k,
+  // the sum taken over the kept stencils in k order.
+  for (int eta = 0; eta < 16; ++eta) {
+    double D = 0.0;
+    for (int k = 0; k < 4; ++k)
+      if (!((eta >> k) & 1)) D = D + d[k];
+    for (int k = 0; k < 4; ++k) wtab[eta][k] = (!((eta >> k) & 1) && D != 0.0) ? d[k] / D : 0.0;
+  }
+}
+
+}  // namespace neno6
+
 namespace {
 
 std::string g_create_error;
@@ -130,35 +164,7 @@ int load_weights(const char* path, NetF64& net, bool& narrow, std::string& msg) 
   return NENO6_OK;
 }
 
-void fill_tables(neno6_handle* h) {
-  if (h->cfg.linear_weights == NENO6_W_SIXTH) {
-    h->d[0] = 9.0 / 20.0;
-    h->d[1] = 3.0 / 10.0;
-    h->d[2] = 1.0 / 20.0;
-    h->d[3] = 1.0 / 5.0;
-  } else {  // Sec. 2.2 / Sec. 4 (TENO6-opt optimal weights)
-    h->d[0] = 0.4294317718960898;
-    h->d[1] = 0.1727270875843552;
-    h->d[2] = 0.0855682281039113;
-    h->d[3] = 0.312272912415645;
-  }
-  // Reconstruction of h(x_{i+1/2}) from point values acting as cell averages
-  // (Eqs. (definitionEq), (approximatepolynomial)) on S0 = {i-1,i,i+1},
-  // S1 = {i,i+1,i+2}, S2 = {i-2,i-1,i}, S3 = {i,i+1,i+2,i+3}.
-  const double c[4][4] = {{-1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
-                          {1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
-                          {1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0},
-                          {1.0 / 4.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0}};
-  std::memcpy(h->cand, c, sizeof c);
-  // Eq. (TENOweight_renormalize): w_k = d_k delta_k / sum_k d_k delta_k,
-  // the sum taken over the kept stencils in k order.
-  for (int eta = 0; eta < 16; ++eta) {
-    double D = 0.0;
-    for (int k = 0; k < 4; ++k)
-      if (!((eta >> k) & 1)) D = D + h->d[k];
-    for (int k = 0; k < 4; ++k) h->wtab[eta][k] = (!((eta >> k) & 1) && D != 0.0) ? h->d[k] / D : 0.0;
-  }
-}
+void fill_tables(neno6_handle* h) { scheme_tables(h->cfg.linear_weights, h->d, h->cand, h->wtab); }
 
 void fill_rhs_args(const neno6_handle* h, RhsArgs& a) {
   std::memset(&a, 0, sizeof a);

@@ -100,6 +100,11 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img);
 // FP32 parameters with every W transposed to [in][out] (guard re-evaluation).
 void build_guard_image(const NetF64& net, float* img);
 
+// Linear weights d_k (printed optimal weights, or the sixth-order test
+// weights), candidate coefficients of S0..S3 and the renormalised weights of
+// every mask pattern: the tables every FP64 launch parameter block carries.
+void scheme_tables(int linear_weights, double d[4], double cand[4][4], double wtab[16][4]);
+
 // Mixed-precision face kernel arguments.
 struct FacesMixedArgs {
   const double* U;

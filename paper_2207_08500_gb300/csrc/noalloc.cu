@@ -3,6 +3,8 @@
 // dt, t and a status word) is one file-scope static device array, created
 // when the library's module is loaded on a device and kept until the process
 // exits.  The kernels are the ones neno6_step launches.
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -21,21 +23,62 @@ constexpr size_t kSmall = 8;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxElems + kSmall];
 
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
+// Per device: the array's device address and the id of the context it was
+// taken in.  A device reset (or a release of the primary context) loads the
+// module again, possibly elsewhere; a changed context id makes the next call
+// look the address up again instead of writing through a stale pointer.
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
+
+// Driver calls reached through the runtime's entry-point query (the library
+// links no driver library): the current context and its process-unique id.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    resolved = true;
+  }
+  CUcontext ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // Device address of the static array on the current device.  The name
 // g_noalloc_scratch is a host-side stand-in in host code, never a device
-// address, so it is looked up once per device with that device current.
+// address, so it is looked up with that device current: once per device and
+// context (every call when the context id cannot be read).
 cudaError_t scratch_address(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+  unsigned long long id = 0;
+  if (g_slot[dev].addr && current_context_id(&id) && id == g_slot[dev].ctx_id) {
+    *out = g_slot[dev].addr;
+    return cudaSuccess;
   }
-  *out = g_scratch_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  // the lookup made the device's primary context current if it was not
+  const bool have_id = current_context_id(&id);
+  g_slot[dev].ctx_id = have_id ? id : 0ull;
+  g_slot[dev].addr = have_id ? static_cast<double*>(p) : nullptr;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -95,23 +138,7 @@ extern "C" int neno6_step_noalloc(const neno6_config* cfg, const double* net_par
   std::memset(&p.a, 0, sizeof p.a);
   std::memcpy(p.net.p, net_params, sizeof p.net.p);
   double d[4];
-  if (c.linear_weights == NENO6_W_SIXTH) {
-    d[0] = 9.0 / 20.0; d[1] = 3.0 / 10.0; d[2] = 1.0 / 20.0; d[3] = 1.0 / 5.0;
-  } else {
-    d[0] = 0.4294317718960898; d[1] = 0.1727270875843552;
-    d[2] = 0.0855682281039113; d[3] = 0.312272912415645;
-  }
-  const double cand[4][4] = {{-1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
-                             {1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0, 0.0},
-                             {1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0},
-                             {1.0 / 4.0, 13.0 / 12.0, -5.0 / 12.0, 1.0 / 12.0}};
-  std::memcpy(p.a.cand, cand, sizeof cand);
-  for (int eta = 0; eta < 16; ++eta) {
-    double D = 0.0;
-    for (int k = 0; k < 4; ++k)
-      if (!((eta >> k) & 1)) D = D + d[k];
-    for (int k = 0; k < 4; ++k) p.a.wtab[eta][k] = (!((eta >> k) & 1) && D != 0.0) ? d[k] / D : 0.0;
-  }
+  scheme_tables(c.linear_weights, d, p.a.cand, p.a.wtab);
   p.a.nx = c.nx;
   p.a.ny = c.ny;
   p.a.bcx = c.bc[0];
