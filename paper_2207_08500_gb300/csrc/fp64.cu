@@ -22,6 +22,7 @@
 // arithmetic.
 #include "fp64_ops.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace neno6 {
 namespace {
@@ -32,17 +33,22 @@ constexpr int kThreads = 256;
 
 template <int NDIM>
 struct Geom;
+// Staged tile: TX x TY cells and a 3-cell halo; staged column bx holds
+// global column i0 - X0 + bx.  In 2D the tile's rows are 40 cells wide
+// (i0-4 .. i0+35) so that a TMA copy of the box can start on a 16-byte
+// boundary (an even float64 column); the outer two columns are staged but
+// never read.
 template <>
 struct Geom<2> {
   static constexpr int TX = 32, TY = 16, HY = 3, NV = 4;
-  static constexpr int SX = TX + 6, SY = TY + 6;
+  static constexpr int X0 = 4, SX = TX + 8, SY = TY + 6;
   static constexpr int NXF = TY * (TX + 1);  // x faces of a tile
   static constexpr int NYF = (TY + 1) * TX;  // y faces of a tile
 };
 template <>
 struct Geom<1> {
   static constexpr int TX = 63, TY = 1, HY = 0, NV = 3;
-  static constexpr int SX = TX + 6, SY = 1;
+  static constexpr int X0 = 3, SX = TX + 6, SY = 1;
   static constexpr int NXF = TX + 1;
   static constexpr int NYF = 0;
 };
@@ -65,9 +71,20 @@ constexpr int kPark = 16;
 template <int NDIM>
 constexpr size_t rhs_smem_bytes() {
   using G = Geom<NDIM>;
+  // ... then one mbarrier (the tile's TMA copy)
   return sizeof(double) * (size_t(CellArrays<G::NV>::N) * G::SX * G::SY +
                            size_t(G::NV) * G::TY * (G::TX + 1) +
-                           size_t(G::NV) * (G::TY + 1) * G::TX + size_t(kPark) * kThreads);
+                           size_t(G::NV) * (G::TY + 1) * G::TX + size_t(kPark) * kThreads + 1);
+}
+
+// The 2D tile at (i0, j0) is copied by TMA: U described by the tensor map
+// (in the parameter space, 64-byte aligned) and the whole staged box inside
+// the grid (no periodic wrap, no clamp).  The box's first column i0 - 4 is
+// even, hence 16-byte aligned.
+__device__ __forceinline__ bool tile_by_tma(const RhsArgs& a, int i0, int j0) {
+  using G = Geom<2>;
+  return a.use_tma && (reinterpret_cast<uintptr_t>(&a.tmap) & 63u) == 0 && i0 - G::X0 >= 0 &&
+         i0 - G::X0 + G::SX <= a.nx && j0 - G::HY >= 0 && j0 - G::HY + G::SY <= a.ny;
 }
 
 template <int NDIM>
@@ -76,11 +93,12 @@ __global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_cons
   using CA = CellArrays<G::NV>;
   constexpr int NV = G::NV, SX = G::SX, SY = G::SY, NC = SX * SY;
   constexpr int TX = G::TX, TY = G::TY;
-  extern __shared__ double smem[];
+  extern __shared__ __align__(1024) double smem[];
   double* C = smem;                        // [CA::N][NC]
   double* sFx = smem + CA::N * NC;         // [NV][TY][TX+1]
   double* sFy = sFx + NV * TY * (TX + 1);  // [NV][TY+1][TX]
   double* park = sFy + NV * (TY + 1) * TX + threadIdx.x;  // [kPark][kThreads]
+  uint64_t* tbar = reinterpret_cast<uint64_t*>(sFy + NV * (TY + 1) * TX + kPark * kThreads);
   const RhsArgs& a = P.a;
   const double* __restrict__ net = P.net.p;
   const int nx = a.nx, ny = a.ny;
@@ -88,17 +106,46 @@ __global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_cons
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const double gm1 = a.gm1, gamma = a.gamma;
 
-  // ---- 1. tile + halo (ghost cells by wrap / clamp) and per-cell quantities
+  // ---- 1. tile + halo and per-cell quantities.  An interior 2D tile's
+  // conserved variables arrive by one TMA copy of the box [NV][SY][SX]
+  // straight into the CA::U planes; edge tiles (ghost cells by periodic wrap
+  // or zero-gradient clamp) and 1D tiles are loaded cell by cell.
+  bool by_tma = false;
+  if (NDIM == 2) {
+    by_tma = tile_by_tma(a, i0, j0);
+    if (by_tma) {
+      if (threadIdx.x == 0) {
+        tc::mbar_init(tbar, 1);
+        tc::fence_mbar_init();
+        tc::mbar_arrive_expect_tx(tbar, (uint32_t)(NV * NC * sizeof(double)));
+        tc::tma_load_3d(C + CA::U * NC, &a.tmap, tbar, i0 - G::X0, j0 - G::HY, 0);
+      }
+      __syncthreads();  // the barrier is initialised before anyone waits on it
+      const bool timed_out = !tc::mbar_wait(tbar, 0);
+      if (__syncthreads_or(timed_out)) {
+        // the copy may still be in flight: wait once more (bounded) before
+        // the CTA's shared memory is released
+        tc::mbar_wait(tbar, 0);
+        if (threadIdx.x == 0) atomicOr(a.status, 4);
+        return;
+      }
+    }
+  }
   for (int e = threadIdx.x; e < NC; e += kThreads) {
     const int bx = e % SX, by = e / SX;
-    const int gi = wrap_index(i0 - 3 + bx, nx, a.bcx);
-    const int gj = NDIM == 2 ? wrap_index(j0 - G::HY + by, ny, a.bcy) : 0;
-    const size_t g = (size_t)gj * nx + gi;
     double U[NV];
+    if (by_tma) {
 #pragma unroll
-    for (int n = 0; n < NV; ++n) {
-      U[n] = a.U[n * plane + g];
-      C[(CA::U + n) * NC + e] = U[n];
+      for (int n = 0; n < NV; ++n) U[n] = C[(CA::U + n) * NC + e];
+    } else {
+      const int gi = wrap_index(i0 - G::X0 + bx, nx, a.bcx);
+      const int gj = NDIM == 2 ? wrap_index(j0 - G::HY + by, ny, a.bcy) : 0;
+      const size_t g = (size_t)gj * nx + gi;
+#pragma unroll
+      for (int n = 0; n < NV; ++n) {
+        U[n] = a.U[n * plane + g];
+        C[(CA::U + n) * NC + e] = U[n];
+      }
     }
     const double rho = U[0], E = U[NV - 1];
     const double u = __ddiv_rn(U[1], rho);
@@ -168,14 +215,14 @@ __global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_cons
     int cb0, stride, gf, gline;
     if (dir == 0) {
       const int r = face / (TX + 1), f = face % (TX + 1);
-      cb0 = (G::HY + r) * SX + f;
+      cb0 = (G::HY + r) * SX + (G::X0 - 3) + f;
       stride = 1;
       gf = i0 + f;      // global face index along x, 0..nx
       gline = j0 + r;   // row
     } else {
       const int fl = face - G::NXF;
       const int f = fl / TX, c = fl % TX;
-      cb0 = f * SX + 3 + c;
+      cb0 = f * SX + G::X0 + c;
       stride = SX;
       gf = j0 + f;
       gline = i0 + c;   // column
@@ -356,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_cons
     const int gi = i0 + c, gj = j0 + r;
     if (gi >= nx || gj >= ny) continue;
     const size_t g = (size_t)gj * nx + gi;
-    const int bc = (G::HY + r) * SX + 3 + c;
+    const int bc = (G::HY + r) * SX + G::X0 + c;
 #pragma unroll
     for (int n = 0; n < NV; ++n) {
       const double Fp = sFx[(n * TY + r) * (TX + 1) + c + 1];
@@ -467,7 +514,46 @@ __global__ void __launch_bounds__(256) cfl_reduce_kernel(const double* __restric
 
 }  // namespace
 
-cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s) {
+namespace {
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry-point
+// query (the library links no driver library); null if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of the 2D state U ([4][ny][nx] float64) with the box of one
+// staged FP64 tile ([4][SY][SX]).  False when U cannot be described: the
+// row stride nx * 8 and the base must be multiples of 16 bytes.
+bool encode_tile_map(RhsArgs& a) {
+  using G = Geom<2>;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || a.nx % 2 != 0 || (reinterpret_cast<uintptr_t>(a.U) & 15u) != 0) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)G::NV};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 8, (cuuint64_t)a.nx * a.ny * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)G::SX, (cuuint32_t)G::SY, (cuuint32_t)G::NV};
+  const cuuint32_t unit[3] = {1, 1, 1};
+  return enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(a.U), dims, strides, box, unit,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_fp64(int ndim, RhsParamsF64& p, cudaStream_t s) {
+  p.a.use_tma = ndim == 2 && encode_tile_map(p.a) ? 1 : 0;
   if (ndim == 2) {
     using G = Geom<2>;
     constexpr size_t sm = rhs_smem_bytes<2>();

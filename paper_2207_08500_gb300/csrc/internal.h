@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace neno6 {
@@ -20,8 +21,13 @@ struct NetF64 {
 // Mask modes (public NENO6_MASK_* plus the frozen-mask mode).
 enum MaskMode { kMaskMLP = 0, kMaskSmooth = 1, kMaskRough = 2, kMaskGiven = 3 };
 
-// Arguments of one RHS / RK3-stage launch.
+// Arguments of one RHS / RK3-stage launch.  The tensor map (filled by
+// launch_rhs_fp64) describes U as a [nv][ny][nx] float64 tensor with the box
+// of one FP64 tile and its halo; use_tma = 0 when U cannot be described (odd
+// nx, 1D) and every tile is loaded with plain loads.
 struct RhsArgs {
+  CUtensorMap tmap;
+  int use_tma;
   const double* U;   // state the right-hand side is evaluated on
   const double* U0;  // state at the start of the RK3 step (stages 2, 3)
   double* out;       // dU/dt (stage 0) or the next stage state
@@ -147,7 +153,7 @@ cudaError_t launch_cfl_mixed(int ndim, const double* U, int nx, int ny, double g
 cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, double dy, double cfl, double t_end,
                       const double* t_dev, double* dt_dev, double* dt_user, cudaStream_t s);
 
-cudaError_t launch_rhs_fp64(int ndim, const RhsParamsF64& p, cudaStream_t s);
+cudaError_t launch_rhs_fp64(int ndim, RhsParamsF64& p, cudaStream_t s);
 cudaError_t launch_classify_mixed(const double* X, long long n, uint8_t* eta, double* logits,
                                   const uint8_t* net_image, bool bf16, bool narrow, int* status,
                                   cudaStream_t s);
