@@ -74,6 +74,13 @@ extern "C" {
 #define NENO6_MASK_MLP 0        /* the classifier decides (the method)     */
 #define NENO6_MASK_ALL_SMOOTH 1 /* keep every stencil: the linear scheme   */
 #define NENO6_MASK_ALL_ROUGH 2  /* discard all: first-order upwind fallback */
+/* TENO6-opt stencil selection of Sec. 2.1-2.2 (Eqs. (measureTENO),
+ * (taukTENO), (normalize), (cut-off); C = 1, q = 6, eps = 1e-40, C_T = 1e-6,
+ * smoothness indicators from the Jiang-Shu definition) on the split
+ * characteristic fluxes, in place of the classifier: the paper's comparison
+ * scheme on the same path.  FP64 handles only (neno6_create refuses it for
+ * the mixed precisions with NENO6_ERR_UNSUPPORTED). */
+#define NENO6_MASK_TENO6 3
 
 typedef struct neno6_config {
   int ndim;           /* 1 or 2                                            */

@@ -28,7 +28,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _SRC = os.path.join(_HERE, "neno6_oracle.cpp")
 
-MASK_MODES = {"mlp": 0, "smooth": 1, "rough": 2, "given": 3}
+MASK_MODES = {"mlp": 0, "smooth": 1, "rough": 2, "given": 3, "teno6": 4}
 BCS = {"periodic": 0, "transmissive": 1}
 
 
@@ -55,7 +55,25 @@ class _Params(ctypes.Structure):
         ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
         ("d", ctypes.c_double * 4), ("cand", (ctypes.c_double * 4) * 4),
         ("net", ctypes.POINTER(ctypes.c_double)),
+        ("teno", ctypes.POINTER(ctypes.c_double)),
     ]
+
+
+_teno_tables = None
+
+
+def teno_tables():
+    """The TENO6-opt smoothness-indicator matrices (S0, S1, S2, S3, full
+    stencil; 79 float64 values) of oracle/train/teno6.py, derived exactly from
+    the Jiang-Shu definition and rounded once."""
+    global _teno_tables
+    if _teno_tables is None:
+        from .train import teno6
+        parts = [teno6.beta_matrix(teno6.STENCILS[k]).ravel() for k in range(4)]
+        parts.append(teno6.beta_matrix(teno6.FULL).ravel())
+        _teno_tables = np.ascontiguousarray(np.concatenate(parts), dtype=np.float64)
+        assert _teno_tables.size == 79
+    return _teno_tables
 
 
 _lib = None
@@ -132,14 +150,24 @@ class Oracle:
             for l in range(4):
                 p.cand[k][l] = cand[k][l]
         p.net = _ptr(self._packed, ctypes.c_double)
+        self._teno = None
         self._p = p
+        if mask_mode == "teno6":
+            self._attach_teno(p)
 
     # -- helpers -----------------------------------------------------------
+    def _attach_teno(self, p):
+        if self._teno is None:
+            self._teno = teno_tables()
+        p.teno = _ptr(self._teno, ctypes.c_double)
+
     def _with_mode(self, mode):
         q = _Params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(self._p), ctypes.sizeof(_Params))
         if mode is not None:
             q.mask_mode = MASK_MODES[mode]
+        if q.mask_mode == MASK_MODES["teno6"]:
+            self._attach_teno(q)
         return q
 
     def mask_size(self):

@@ -98,20 +98,25 @@ struct OracleParams {
   int ndim;         // 1 or 2
   int nx, ny;       // interior cells (ny = 1 in 1D)
   int bc_x, bc_y;   // 0 = periodic, 1 = transmissive (zero-gradient)
-  int mask_mode;    // 0 = MLP, 1 = all smooth, 2 = all discarded, 3 = given
+  int mask_mode;    // 0 = MLP, 1 = all smooth, 2 = all discarded, 3 = given,
+                    // 4 = TENO6-opt selection
   int n_layers;     // affine layers of the classifier (5 for 6-64-32-16-8-4)
   int widths[8];    // widths[0] = 6 inputs ... widths[n_layers] = 4 outputs
   double dx, dy, gamma;
   double d[4];        // optimal linear weights d_0..d_3
   double cand[4][4];  // candidate coefficients; S0..S2 use the first three
   const double* net;  // per layer: W[out][in] row-major, then b[out]
+  // TENO6-opt smoothness indicators (mask_mode 4): beta = v^T B v with B for
+  // S0, S1, S2 (3 x 3 each), S3 (4 x 4), the full stencil (6 x 6), row-major,
+  // 79 values; v = the stencil's values minus its first value
+  const double* teno;
 };
 
 }  // extern "C"
 
 namespace {
 
-enum { MASK_MLP = 0, MASK_SMOOTH = 1, MASK_ROUGH = 2, MASK_GIVEN = 3 };
+enum { MASK_MLP = 0, MASK_SMOOTH = 1, MASK_ROUGH = 2, MASK_GIVEN = 3, MASK_TENO = 4 };
 
 // ------------------------------------------------------ Sec. 3.1 classifier
 // Eq. (normalizainput) then Eqs. (reconstuction)/(activationfunction); returns
@@ -150,6 +155,67 @@ unsigned classify6(const OracleParams& P, const double s[6], double* logits_out)
     if (logits_out) logits_out[k] = x[k];
     if (x[k] > 0.0) eta |= 1u << k;
   }
+  return eta;
+}
+
+// -------------------------------------------- Sec. 2.1-2.2 TENO6-opt selection
+// beta = v^T B v (an integral of squared derivatives: a value that rounds
+// below 0 is 0), summed row by row in index order.
+double quad_form(const double* B, const double* v, int r) {
+  double s = 0.0;
+  for (int i = 0; i < r; ++i) {
+    double row = 0.0;
+    for (int j = 0; j < r; ++j) row = row + B[i * r + j] * v[j];
+    s = s + v[i] * row;
+  }
+  return s > 0.0 ? s : 0.0;
+}
+
+// TENO6-opt stencil selection on the six values s (i-2..i+3), returned as
+// eta bits (bit k set <=> S_k discarded):
+//   beta_k of S0..S3 and beta_6 of the full stencil (Jiang-Shu definition);
+//   tau_6 = |beta_6 - (beta_1 + beta_2 + 4 beta_0) / 6|    Eq. (taukTENO)
+//   gamma_k = (C + tau_6 / (beta_k + eps))^q, C = 1, q = 6, eps = 1e-40
+//                                                          Eq. (measureTENO)
+//   chi_k = gamma_k / sum gamma                            Eq. (normalize)
+//   delta_k = [chi_k >= C_T], C_T = 1e-6                   Eq. (cut-off)
+// gamma_k / gamma_max = (a_k / a_max)^6 with a_k = C + tau_6 / (beta_k + eps)
+// (three multiplications) replaces gamma_k in the ratio chi_k: the same
+// quotient, without overflow when some beta_k is 0.
+unsigned teno6_eta(const OracleParams& P, const double s[6]) {
+  static const int cells[4][4] = {{1, 2, 3, 0}, {2, 3, 4, 0}, {0, 1, 2, 0}, {2, 3, 4, 5}};
+  const double* B3 = P.teno;
+  const double* B4 = P.teno + 27;
+  const double* B6 = P.teno + 43;
+  double beta[4], v[6];
+  for (int k = 0; k < 3; ++k) {
+    for (int j = 0; j < 3; ++j) v[j] = s[cells[k][j]] - s[cells[k][0]];
+    beta[k] = quad_form(B3 + 9 * k, v, 3);
+  }
+  for (int j = 0; j < 4; ++j) v[j] = s[cells[3][j]] - s[cells[3][0]];
+  beta[3] = quad_form(B4, v, 4);
+  for (int j = 0; j < 6; ++j) v[j] = s[j] - s[0];
+  const double beta6 = quad_form(B6, v, 6);
+  double t = beta[1] + beta[2];
+  t = t + 4.0 * beta[0];
+  t = t / 6.0;
+  const double tau = std::fabs(beta6 - t);
+  double a[4], amax = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    a[k] = 1.0 + tau / (beta[k] + 1e-40);
+    amax = k == 0 ? a[k] : std::fmax(amax, a[k]);
+  }
+  double g[4], sum = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const double b = a[k] / amax;
+    const double b2 = b * b;
+    const double b3 = b2 * b;
+    g[k] = b3 * b3;
+    sum = sum + g[k];
+  }
+  unsigned eta = 0;
+  for (int k = 0; k < 4; ++k)
+    if (!(g[k] / sum >= 1e-6)) eta |= 1u << k;
   return eta;
 }
 
@@ -395,8 +461,13 @@ bool face_flux(const OracleParams& P, int dir, const Cell<T> st[6], uint8_t* eta
         xp[j] = val(sp[j]);
         xm[j] = val(sneg[j]);
       }
-      ep = classify6(P, xp, nullptr);
-      em = classify6(P, xm, nullptr);
+      if (P.mask_mode == MASK_TENO) {
+        ep = teno6_eta(P, xp);
+        em = teno6_eta(P, xm);
+      } else {
+        ep = classify6(P, xp, nullptr);
+        em = classify6(P, xm, nullptr);
+      }
     }
     if (eta_io && P.mask_mode != MASK_GIVEN) eta_io[m] = (uint8_t)(ep | (em << 4));
     T gp = combine(P, sp, ep);
@@ -636,6 +707,8 @@ double oracle_reconstruct(const OracleParams* P, const double s[6], uint8_t* eta
     eta = 0u;
   else if (P->mask_mode == MASK_ROUGH)
     eta = 15u;
+  else if (P->mask_mode == MASK_TENO)
+    eta = teno6_eta(*P, s);
   else
     eta = classify6(*P, s, nullptr);
   if (eta_io) *eta_io = (uint8_t)eta;
@@ -729,7 +802,10 @@ static void scalar_rhs(const OracleParams& P, int law, const std::vector<double>
     unsigned ep, em;
     if (P.mask_mode == MASK_SMOOTH) ep = em = 0u;
     else if (P.mask_mode == MASK_ROUGH) ep = em = 15u;
-    else {
+    else if (P.mask_mode == MASK_TENO) {
+      ep = teno6_eta(P, sp);
+      em = teno6_eta(P, sneg);
+    } else {
       ep = classify6(P, sp, nullptr);
       em = classify6(P, sneg, nullptr);
     }

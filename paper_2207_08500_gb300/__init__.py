@@ -22,7 +22,7 @@ PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}
 BC = {"periodic": 0, "transmissive": 1}
 LINEAR_WEIGHTS = {"paper": 0, "sixth": 1}
 DATAGEN_DRAWS = 9  # uniform draws per training sample (neno6_datagen)
-MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2}
+MASK_MODE = {"mlp": 0, "smooth": 1, "rough": 2, "teno6": 3}
 LAW = {"advection": 0, "burgers": 1}
 # logit band re-evaluated in FP32 by the mixed-precision path
 DEFAULT_GUARD_TAU = {"fp64": 0.0, "bf16": 1.0, "fp16": 0.5}

@@ -2,11 +2,13 @@
 // cycle, weights-file loading, argument checks and kernel launches.  Nothing
 // here throws across the ABI; errors are returned as NENO6_ERR_* codes with a
 // message kept on the handle.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/neno6.h"
@@ -47,6 +49,120 @@ struct neno6_handle {
 };
 
 namespace neno6 {
+
+namespace {
+
+// Exact rational arithmetic for the TENO6-opt indicator matrices (small
+// numerators and denominators: the six-point matrix's largest denominator
+// is 120960), reduced after every operation.
+struct Rat {
+  __int128 n, d;
+};
+__int128 gcd128(__int128 a, __int128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b != 0) {
+    const __int128 r = a % b;
+    a = b;
+    b = r;
+  }
+  return a;
+}
+Rat rat(__int128 n, __int128 d) {
+  if (d < 0) {
+    n = -n;
+    d = -d;
+  }
+  const __int128 g = gcd128(n, d);
+  if (g > 1) {
+    n /= g;
+    d /= g;
+  }
+  return Rat{n, d};
+}
+Rat operator+(Rat a, Rat b) { return rat(a.n * b.d + b.n * a.d, a.d * b.d); }
+Rat operator-(Rat a, Rat b) { return rat(a.n * b.d - b.n * a.d, a.d * b.d); }
+Rat operator*(Rat a, Rat b) { return rat(a.n * b.n, a.d * b.d); }
+Rat operator/(Rat a, Rat b) { return rat(a.n * b.d, a.d * b.n); }
+// Correctly rounded binary64 value: numerator and denominator are exact
+// doubles (below 2^53), and IEEE division rounds their quotient once.
+double to_double(Rat a) {
+  const __int128 lim = (__int128)1 << 53;
+  if (a.n >= lim || -a.n >= lim || a.d >= lim) return std::nan("");
+  return (double)(long long)a.n / (double)(long long)a.d;
+}
+
+// B with beta = f^T B f for the cells at offsets o[0..r-1] (unit spacing,
+// the central cell at 0): the polynomial p of degree r-1 whose cell averages
+// are f has coefficients a = A^-1 f, A_jl = integral of x^l over cell o_j;
+// the Jiang-Shu indicator sum_{l=1}^{r-1} integral over [-1/2, 1/2] of
+// (d^l p / dx^l)^2 is then a^T M a.
+void beta_rational(const int* o, int r, double* out) {
+  Rat A[6][12];
+  for (int j = 0; j < r; ++j) {
+    const Rat hi = rat(2 * o[j] + 1, 2), lo = rat(2 * o[j] - 1, 2);
+    Rat ph = hi, pl = lo;  // hi^(l+1), lo^(l+1)
+    for (int l = 0; l < r; ++l) {
+      A[j][l] = (ph - pl) / rat(l + 1, 1);
+      ph = ph * hi;
+      pl = pl * lo;
+    }
+    for (int l = 0; l < r; ++l) A[j][r + l] = rat(j == l ? 1 : 0, 1);
+  }
+  for (int c = 0; c < r; ++c) {  // Gauss-Jordan: [A | I] -> [I | A^-1]
+    int piv = c;
+    while (A[piv][c].n == 0) ++piv;
+    if (piv != c)
+      for (int l = 0; l < 2 * r; ++l) std::swap(A[c][l], A[piv][l]);
+    const Rat d = A[c][c];
+    for (int l = 0; l < 2 * r; ++l) A[c][l] = A[c][l] / d;
+    for (int j = 0; j < r; ++j) {
+      if (j == c || A[j][c].n == 0) continue;
+      const Rat f = A[j][c];
+      for (int l = 0; l < 2 * r; ++l) A[j][l] = A[j][l] - f * A[c][l];
+    }
+  }
+  // M_pq = sum_l p!/(p-l)! q!/(q-l)! integral of x^(p+q-2l) over [-1/2, 1/2]
+  Rat M[6][6];
+  for (int p = 0; p < r; ++p)
+    for (int q = 0; q < r; ++q) {
+      M[p][q] = rat(0, 1);
+      for (int l = 1; l <= p && l <= q; ++l) {
+        const int m = p + q - 2 * l;
+        if (m % 2) continue;
+        __int128 fp = 1, fq = 1;
+        for (int t = 0; t < l; ++t) {
+          fp *= p - t;
+          fq *= q - t;
+        }
+        M[p][q] = M[p][q] + rat(fp * fq, ((__int128)1 << m) * (m + 1));
+      }
+    }
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < r; ++j) {
+      Rat b = rat(0, 1);
+      for (int p = 0; p < r; ++p)
+        for (int q = 0; q < r; ++q) b = b + A[p][r + i] * M[p][q] * A[q][r + j];
+      out[i * r + j] = to_double(b);
+    }
+}
+
+}  // namespace
+
+void teno_tables(double out[kTenoTable]) {
+  static const std::vector<double> t = [] {
+    std::vector<double> x(kTenoTable);
+    const int s0[3] = {-1, 0, 1}, s1[3] = {0, 1, 2}, s2[3] = {-2, -1, 0}, s3[4] = {0, 1, 2, 3};
+    const int full[6] = {-2, -1, 0, 1, 2, 3};
+    beta_rational(s0, 3, &x[0]);
+    beta_rational(s1, 3, &x[9]);
+    beta_rational(s2, 3, &x[18]);
+    beta_rational(s3, 4, &x[27]);
+    beta_rational(full, 6, &x[43]);
+    return x;
+  }();
+  std::memcpy(out, t.data(), sizeof(double) * kTenoTable);
+}
 
 void scheme_tables(int linear_weights, double d[4], double cand[4][4], double wtab[16][4]) {
   if (linear_weights == NENO6_W_SIXTH) {
@@ -182,6 +298,7 @@ void fill_rhs_args(const neno6_handle* h, RhsArgs& a) {
   a.status = h->d_status;
   std::memcpy(a.cand, h->cand, sizeof a.cand);
   std::memcpy(a.wtab, h->wtab, sizeof a.wtab);
+  if (a.mask_mode == kMaskTeno) teno_tables(a.teno);
 }
 
 size_t face_elems(const neno6_handle* h) {
@@ -272,10 +389,12 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
       return fail(nullptr, NENO6_ERR_ARG, "bad boundary condition");
   if (c.linear_weights != NENO6_W_PAPER_OPT && c.linear_weights != NENO6_W_SIXTH)
     return fail(nullptr, NENO6_ERR_ARG, "bad linear_weights");
-  if (c.mask_mode < NENO6_MASK_MLP || c.mask_mode > NENO6_MASK_ALL_ROUGH)
+  if (c.mask_mode < NENO6_MASK_MLP || c.mask_mode > NENO6_MASK_TENO6)
     return fail(nullptr, NENO6_ERR_ARG, "bad mask_mode");
   if (c.precision != NENO6_FP64 && c.precision != NENO6_MIXED_BF16 && c.precision != NENO6_MIXED_FP16)
     return fail(nullptr, NENO6_ERR_ARG, "bad precision");
+  if (c.mask_mode == NENO6_MASK_TENO6 && c.precision != NENO6_FP64)
+    return fail(nullptr, NENO6_ERR_UNSUPPORTED, "the TENO6-opt mask mode needs the FP64 path");
 
   neno6_handle* h = new (std::nothrow) neno6_handle();
   if (!h) return fail(nullptr, NENO6_ERR_ARG, "out of host memory");

@@ -18,7 +18,8 @@
 // strictly between the outermost cell centres of S_k; family 9 by the
 // TENO6-opt selection of Sec. 2 (Eqs. (measureTENO), (taukTENO),
 // (normalize), (cut-off); C = 1, q = 6, eps = 1e-40, C_T = 1e-6), with
-// smoothness indicators from the Jiang-Shu definition.  Output values are
+// smoothness indicators from the Jiang-Shu definition (the selection the
+// FP64 right-hand side uses in its TENO6-opt mask mode).  Output values are
 // normalised by Eq. (normalizainput).
 //
 // This unit is compiled with -fmad=false and evaluates every expression in
@@ -29,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "fp64_ops.cuh"
 #include "internal.h"
 
 namespace neno6 {
@@ -37,131 +39,19 @@ namespace {
 constexpr int kDraws = 9;
 constexpr int kThreads = 256;
 
-// Smoothness-indicator quadratic forms: beta = v^T B v over the stencil's
-// values v (each taken relative to the stencil's first value).
+// TENO6-opt indicator matrices (exact rationals rounded once), passed by
+// value as a kernel parameter.
 struct TenoTables {
-  double b3[3][9];  // S_0 {i-1,i,i+1}, S_1 {i,i+1,i+2}, S_2 {i-2,i-1,i}
-  double b4[16];    // S_3 {i..i+3}
-  double b6[36];    // the full stencil i-2..i+3
+  double t[kTenoTable];
 };
 
-// B for cell offsets o[0..r-1] (unit spacing, cell i centred at 0):
-// the degree r-1 polynomial with the given cell averages has coefficients
-// a = A^-1 v, A_jl = mean of x^l over cell o_j; beta = sum over l = 1..r-1
-// of the integral over the central cell of (d^l p / dx^l)^2 = a^T M a.
-void beta_matrix(const int* o, int r, double* B) {
-  double A[6][12];
-  for (int j = 0; j < r; ++j) {
-    for (int l = 0; l < r; ++l) {
-      const double hi = o[j] + 0.5, lo = o[j] - 0.5;
-      A[j][l] = (std::pow(hi, l + 1) - std::pow(lo, l + 1)) / (l + 1);
-    }
-    for (int l = 0; l < r; ++l) A[j][r + l] = j == l ? 1.0 : 0.0;
-  }
-  // Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
-  for (int c = 0; c < r; ++c) {
-    int piv = c;
-    for (int j = c + 1; j < r; ++j)
-      if (std::fabs(A[j][c]) > std::fabs(A[piv][c])) piv = j;
-    if (piv != c)
-      for (int l = 0; l < 2 * r; ++l) std::swap(A[c][l], A[piv][l]);
-    const double d = A[c][c];
-    for (int l = 0; l < 2 * r; ++l) A[c][l] /= d;
-    for (int j = 0; j < r; ++j) {
-      if (j == c) continue;
-      const double f = A[j][c];
-      for (int l = 0; l < 2 * r; ++l) A[j][l] -= f * A[c][l];
-    }
-  }
-  // M_pq = sum_l (p!/(p-l)!) (q!/(q-l)!) * integral of x^(p+q-2l) over [-1/2, 1/2]
-  auto falling = [](int p, int l) {
-    double f = 1.0;
-    for (int t = 0; t < l; ++t) f *= (p - t);
-    return f;
-  };
-  double M[6][6] = {};
-  for (int p = 0; p < r; ++p)
-    for (int q = 0; q < r; ++q)
-      for (int l = 1; l < r; ++l) {
-        if (l > p || l > q) continue;
-        const int m = p + q - 2 * l;
-        if (m % 2) continue;
-        M[p][q] += falling(p, l) * falling(q, l) * (2.0 * std::pow(0.5, m + 1) / (m + 1));
-      }
-  // B = (A^-1)^T M A^-1
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < r; ++j) {
-      double s = 0.0;
-      for (int p = 0; p < r; ++p)
-        for (int q = 0; q < r; ++q) s += A[p][r + i] * M[p][q] * A[q][r + j];
-      B[i * r + j] = s;
-    }
-}
-
-const TenoTables& teno_tables() {
-  static const TenoTables t = [] {
-    TenoTables x{};
-    const int s0[3] = {-1, 0, 1}, s1[3] = {0, 1, 2}, s2[3] = {-2, -1, 0}, s3[4] = {0, 1, 2, 3};
-    const int full[6] = {-2, -1, 0, 1, 2, 3};
-    beta_matrix(s0, 3, x.b3[0]);
-    beta_matrix(s1, 3, x.b3[1]);
-    beta_matrix(s2, 3, x.b3[2]);
-    beta_matrix(s3, 4, x.b4);
-    beta_matrix(full, 6, x.b6);
-    return x;
-  }();
-  return t;
-}
-
-// positions (0..5 = cells i-2..i+3) of the candidate sub-stencils; the
-// outermost cell offsets of S_k are kSpan[k]
-__constant__ int kCells[4][4] = {{1, 2, 3, -1}, {2, 3, 4, -1}, {0, 1, 2, -1}, {2, 3, 4, 5}};
+// outermost cell offsets of the candidate sub-stencils S_k
 __constant__ int kSpan[4][2] = {{-1, 1}, {0, 2}, {-2, 0}, {0, 3}};
 
 __device__ double ipow(double b, int k) {
   double r = b;
   for (int t = 1; t < k; ++t) r = r * b;
   return r;
-}
-
-template <int R>
-__device__ double quad_form(const double* B, const double* v) {
-  double s = 0.0;
-  for (int i = 0; i < R; ++i) {
-    double row = 0.0;
-    for (int j = 0; j < R; ++j) row = row + B[i * R + j] * v[j];
-    s = s + v[i] * row;
-  }
-  return s > 0.0 ? s : 0.0;  // an integral of squares: rounding below 0 is 0
-}
-
-// TENO6-opt labels (1 = sub-stencil discarded) of the six values f.
-__device__ unsigned teno_labels(const TenoTables& T, const double* f) {
-  double beta[4], v[6];
-  for (int k = 0; k < 3; ++k) {
-    for (int j = 0; j < 3; ++j) v[j] = f[kCells[k][j]] - f[kCells[k][0]];
-    beta[k] = quad_form<3>(T.b3[k], v);
-  }
-  for (int j = 0; j < 4; ++j) v[j] = f[kCells[3][j]] - f[kCells[3][0]];
-  beta[3] = quad_form<4>(T.b4, v);
-  for (int j = 0; j < 6; ++j) v[j] = f[j] - f[0];
-  const double b6 = quad_form<6>(T.b6, v);
-  const double tau = fabs(b6 - (beta[1] + beta[2] + 4.0 * beta[0]) / 6.0);
-  // gamma_k = (C + tau / (beta_k + eps))^q, normalised: in the log domain
-  double lg[4], mx = -INFINITY;
-  for (int k = 0; k < 4; ++k) {
-    lg[k] = 6.0 * log(1.0 + tau / (beta[k] + 1e-40));
-    mx = fmax(mx, lg[k]);
-  }
-  double g[4], sum = 0.0;
-  for (int k = 0; k < 4; ++k) {
-    g[k] = exp(lg[k] - mx);
-    sum = sum + g[k];
-  }
-  unsigned eta = 0;
-  for (int k = 0; k < 4; ++k)
-    if (!(g[k] / sum >= 1e-6)) eta |= 1u << k;
-  return eta;
 }
 
 __global__ void __launch_bounds__(kThreads) datagen_kernel(const double* __restrict__ u, long long n,
@@ -252,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) datagen_kernel(const double* __restr
         if (hit) eta |= 1u << k;
       }
     } else if (f == 9) {
-      eta = teno_labels(T, F);
+      eta = f64ops::teno6_eta(T.t, F);
     }
     const double sg = q[8] < 0.5 ? -1.0 : 1.0;
     double m = 1.0;
@@ -272,7 +162,9 @@ cudaError_t launch_datagen(const double* u, long long n, double* X, uint8_t* lab
                            int* status, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const long long blocks = std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 64);
-  datagen_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(u, n, X, labels, family, status, teno_tables());
+  TenoTables T;
+  teno_tables(T.t);
+  datagen_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(u, n, X, labels, family, status, T);
   return cudaGetLastError();
 }
 

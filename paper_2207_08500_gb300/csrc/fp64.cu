@@ -346,6 +346,16 @@ __global__ void __launch_bounds__(kThreads, 1) rhs_fp64_kernel(const __grid_cons
         normalise6(st, x);
         eta_side[side] = mlp64(net, x, z);
       }
+    } else if (a.mask_mode == kMaskTeno) {
+      // TENO6-opt selection on the split fluxes themselves (its indicator
+      // ratios do not depend on the scale)
+#pragma unroll 1
+      for (int side = 0; side < 2; ++side) {
+        double st[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) st[j] = park[(side * 6 + j) * kThreads];
+        eta_side[side] = teno6_eta(a.teno, st);
+      }
     } else if (a.mask_mode == kMaskGiven) {
       size_t idx;
       if (dir == 0) idx = ((size_t)m * ny + gline) * (nx + 1) + gf;

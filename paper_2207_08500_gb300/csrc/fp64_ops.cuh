@@ -29,6 +29,69 @@ __device__ __forceinline__ int wrap_index(int i, int n, int bc) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// beta = v^T B v, summed row by row in index order (an integral of squared
+// derivatives: a value that rounds below 0 is 0).
+template <int R>
+__device__ __forceinline__ double quad_form_rn(const double* __restrict__ B, const double* v) {
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    double row = 0.0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) row = __dadd_rn(row, __dmul_rn(B[i * R + j], v[j]));
+    s = __dadd_rn(s, __dmul_rn(v[i], row));
+  }
+  return s > 0.0 ? s : 0.0;
+}
+
+// TENO6-opt stencil selection (Sec. 2.1-2.2) on the six values s (i-2..i+3),
+// returned as eta bits (bit k set <=> S_k discarded):
+//   tau_6 = |beta_6 - (beta_1 + beta_2 + 4 beta_0) / 6|      Eq. (taukTENO)
+//   gamma_k = (1 + tau_6 / (beta_k + 1e-40))^6               Eq. (measureTENO)
+//   chi_k = gamma_k / sum gamma, delta_k = [chi_k >= 1e-6]   Eqs. (normalize), (cut-off)
+// with gamma_k / gamma_max = (a_k / a_max)^6 (three multiplications) in
+// the ratio, which cannot overflow.  T: the kTenoTable indicator matrices.
+__device__ __forceinline__ unsigned teno6_eta(const double* __restrict__ T, const double s[6]) {
+  double beta[4], v[6];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int c0 = k == 0 ? 1 : (k == 1 ? 2 : 0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v[j] = __dsub_rn(s[c0 + j], s[c0]);
+    beta[k] = quad_form_rn<3>(T + 9 * k, v);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = __dsub_rn(s[2 + j], s[2]);
+  beta[3] = quad_form_rn<4>(T + 27, v);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) v[j] = __dsub_rn(s[j], s[0]);
+  const double beta6 = quad_form_rn<6>(T + 43, v);
+  double t = __dadd_rn(beta[1], beta[2]);
+  t = __dadd_rn(t, __dmul_rn(4.0, beta[0]));
+  t = __ddiv_rn(t, 6.0);
+  const double tau = dabs(__dsub_rn(beta6, t));
+  double a[4], amax = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = __dadd_rn(1.0, __ddiv_rn(tau, __dadd_rn(beta[k], 1e-40)));
+    amax = k == 0 ? a[k] : dmax_nn(amax, a[k]);
+  }
+  double g[4], sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double b = __ddiv_rn(a[k], amax);
+    const double b2 = __dmul_rn(b, b);
+    const double b3 = __dmul_rn(b2, b);
+    g[k] = __dmul_rn(b3, b3);
+    sum = __dadd_rn(sum, g[k]);
+  }
+  unsigned eta = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (!(__ddiv_rn(g[k], sum) >= 1e-6)) eta |= 1u << k;
+  return eta;
+}
+
 // Classifier 6-64-32-16-8-4 of Sec. 3.1 on a normalised stencil.  Eq.
 // (reconstuction): every output of a layer is its bias followed by an fma
 // chain over the layer's inputs in ascending order; ReLU (Eq.

@@ -19,7 +19,15 @@ struct NetF64 {
 };
 
 // Mask modes (public NENO6_MASK_* plus the frozen-mask mode).
-enum MaskMode { kMaskMLP = 0, kMaskSmooth = 1, kMaskRough = 2, kMaskGiven = 3 };
+enum MaskMode { kMaskMLP = 0, kMaskSmooth = 1, kMaskRough = 2, kMaskTeno = 3, kMaskGiven = 4 };
+
+// TENO6-opt smoothness indicators (Sec. 2.1, Jiang-Shu definition): beta =
+// v^T B v with v the stencil's values minus its first value; B of S0, S1, S2
+// (3 x 3 each, offsets 0, 9, 18), S3 (4 x 4, offset 27) and the six-point
+// stencil (6 x 6, offset 43), row-major.  Each entry is the exact rational
+// value rounded once to binary64.
+constexpr int kTenoTable = 79;
+void teno_tables(double out[kTenoTable]);
 
 // Arguments of one RHS / RK3-stage launch.  The tensor map (filled by
 // launch_rhs_fp64) describes U as a [nv][ny][nx] float64 tensor with the box
@@ -46,6 +54,7 @@ struct RhsArgs {
   double third, two_thirds;
   double cand[4][4];   // candidate coefficients, stencil order
   double wtab[16][4];  // renormalised weights d_k / sum(kept d) per mask
+  double teno[kTenoTable];  // TENO6-opt indicator matrices (mask_mode kMaskTeno)
 };
 
 struct RhsParamsF64 {

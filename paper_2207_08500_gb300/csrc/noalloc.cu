@@ -101,7 +101,7 @@ extern "C" int neno6_step_noalloc(const neno6_config* cfg, const double* net_par
   for (int k = 0; k < 2; ++k)
     if (c.bc[k] != NENO6_BC_PERIODIC && c.bc[k] != NENO6_BC_TRANSMISSIVE) return NENO6_ERR_ARG;
   if (c.linear_weights != NENO6_W_PAPER_OPT && c.linear_weights != NENO6_W_SIXTH) return NENO6_ERR_ARG;
-  if (c.mask_mode < NENO6_MASK_MLP || c.mask_mode > NENO6_MASK_ALL_ROUGH) return NENO6_ERR_ARG;
+  if (c.mask_mode < NENO6_MASK_MLP || c.mask_mode > NENO6_MASK_TENO6) return NENO6_ERR_ARG;
   if (n_params != kNetParams) return NENO6_ERR_WEIGHTS;
   if (!aligned16(U)) return NENO6_ERR_ALIGN;
   if (!(cfl > 0.0) || !(t_end >= 0.0)) return NENO6_ERR_ARG;
@@ -150,6 +150,7 @@ extern "C" int neno6_step_noalloc(const neno6_config* cfg, const double* net_par
   p.a.third = 1.0 / 3.0;
   p.a.two_thirds = 2.0 / 3.0;
   p.a.mask_mode = c.mask_mode;
+  if (c.mask_mode == kMaskTeno) teno_tables(p.a.teno);
   p.a.status = status;
   p.a.smax = smax;
   p.a.dt_dev = dt_s;

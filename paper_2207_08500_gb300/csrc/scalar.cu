@@ -45,6 +45,9 @@ __global__ void __launch_bounds__(128) scalar_faces_kernel(const __grid_constant
     ep = em = 0u;
   } else if (P.a.mask_mode == kMaskRough) {
     ep = em = 15u;
+  } else if (P.a.mask_mode == kMaskTeno) {
+    ep = teno6_eta(P.a.teno, sp);
+    em = teno6_eta(P.a.teno, sn);
   } else {
     double x[6], z[4];
     normalise6(sp, x);

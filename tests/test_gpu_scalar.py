@@ -41,7 +41,7 @@ def _initial(n, kind, seed):
 
 
 @pytest.mark.parametrize("law", ["advection", "burgers"])
-@pytest.mark.parametrize("mode", ["mlp", "smooth", "rough"])
+@pytest.mark.parametrize("mode", ["mlp", "smooth", "rough", "teno6"])
 @pytest.mark.parametrize("n,bc,kind", [(400, "periodic", "sine"), (400, "transmissive", "pulse"),
                                        (37, "periodic", "pulse")])
 def test_scalar_solve_bit_exact(lib, oracle_mod, net_file, law, mode, n, bc, kind):

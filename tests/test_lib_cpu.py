@@ -89,3 +89,18 @@ def test_create_rejects_other_network_widths(lib_path, tmp_path):
         h = ctypes.c_void_p()
         assert lib.neno6_create(ctypes.byref(c), str(path).encode(), ctypes.byref(h)) == -4
         assert b"6-64-32-16-8-4" in lib.neno6_last_error(None)
+
+
+def test_create_refuses_teno6_mask_on_mixed_precision(lib_path):
+    """The TENO6-opt mask mode runs on the FP64 path only: a mixed-precision
+    handle with it is refused (NENO6_ERR_UNSUPPORTED) before any device work."""
+    import paper_2207_08500_gb300 as p
+    lib = p.load_library(lib_path)
+    c = p._Config()
+    c.ndim, c.nx, c.ny, c.dx, c.dy, c.gamma = 2, 8, 8, 0.1, 0.1, 1.4
+    c.mask_mode = p.MASK_MODE["teno6"]
+    for prec in ("bf16", "fp16"):
+        c.precision = p.PRECISION[prec]
+        h = ctypes.c_void_p()
+        assert lib.neno6_create(ctypes.byref(c), b"/nonexistent", ctypes.byref(h)) == -8
+        assert b"TENO6" in lib.neno6_last_error(None)
