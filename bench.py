@@ -80,6 +80,50 @@ def fp64_flops_per_cell_rhs_mixed(ndim=2):
     return per_cell + ndim * per_face + nv * 9
 
 
+def mlp_flops_per_cell_rhs(ndim=2):
+    """Algorithmic classifier flops of one cell's RHS: 2 x nv x ndim
+    classifier calls (faces per cell x fields x sides) of 3104 multiply-adds."""
+    nv = 4 if ndim == 2 else 3
+    return 2 * nv * ndim * 2 * (6 * 64 + 64 * 32 + 32 * 16 + 16 * 8 + 8 * 4)
+
+
+def tensor_peak_tflops():
+    """Dense 16-bit tensor-core rate (fp16 and bf16 run at the same rate):
+    the sustained cuBLAS figure of MEASURED_PEAKS.json (the kernel runs inside
+    a long step), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops_sustained"])
+        return v, "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, seconds-long loop)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback: 1.7 PFLOP/s dense bf16 sustained"
+
+
+def gpu_numa_cpus(dev_index):
+    """(node, CPUs) of the NUMA node next to the GPU from sysfs, or None."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(dev_index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        with open("/sys/bus/pci/devices/%s/numa_node" % bus) as f:
+            node = int(f.read())
+        if node < 0:
+            return None
+        with open("/sys/devices/system/node/node%d/cpulist" % node) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return (node, cpus) if cpus else None
+    except Exception:
+        return None
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -194,13 +238,30 @@ def run_ours(args, rank, world):
     # end to end through the C ABI with host buffers: every step one
     # neno6_step_host call, which copies the (pinned) host state to the
     # device, steps it, copies the new state back and synchronises
-    host = torch.from_numpy(U0.copy()).pin_memory()
-    out_host = torch.empty_like(host).pin_memory()
+    numa = gpu_numa_cpus(dev.index)
+    prev_aff = os.sched_getaffinity(0) if numa else None
+    if numa:
+        # the pinned buffers' pages are placed by the allocating thread: on
+        # the NUMA node next to the GPU
+        os.sched_setaffinity(0, numa[1])
+    try:
+        host = torch.from_numpy(U0.copy()).pin_memory()
+        out_host = torch.empty_like(host).pin_memory()
+        out_host.copy_(host)
+    finally:
+        if prev_aff:
+            os.sched_setaffinity(0, prev_aff)
     solver.step_host(host, cfl, out=out_host)  # allocates the call's device state
     torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    U.copy_(host, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = host.numel() * 8 / (h0.elapsed_time(h1) * 1e-3) / 1e9
     barrier()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     f0.record(stream)
     for _ in range(e2e_steps):
         solver.step_host(host, cfl, out=out_host)
@@ -229,18 +290,25 @@ def run_ours(args, rank, world):
         A, B = S0.clone(), S0.clone()
         ta = torch.zeros(1, dtype=torch.float64, device=dev)
         tb = torch.zeros(1, dtype=torch.float64, device=dev)
-        ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        ev64[0].record(stream)
+        # one RK3 step of each path from the same state: the state error
         ref.step(A, cfl, t=ta)
-        ev64[1].record(stream)
         solver.step(B, cfl, t=tb)
         torch.cuda.synchronize()
-        fp64_ms = ev64[0].elapsed_time(ev64[1])
         st_l1 = ((B - A).abs().sum() / A.abs().sum()).item()
         st_linf = ((B - A).abs().max() / A.abs().max()).item()
+        # FP64 path speed: that step was its warm-up; three more timed
+        fp64_steps = 3
+        ev64 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev64[0].record(stream)
+        for _ in range(fp64_steps):
+            ref.step(A, cfl, t=ta)
+        ev64[1].record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = ev64[0].elapsed_time(ev64[1]) / fp64_steps
         compare = {
             "fp64_gpu_value": round(n * n / (fp64_ms * 1e-3) / 1e6, 4), "unit": UNIT,
             "fp64_gpu_ms_per_step": round(fp64_ms, 3),
+            "fp64_gpu_timing": "mean of %d SSP-RK3 steps after one untimed step" % fp64_steps,
             "mask_flip_rate": flips / (8.0 * m64.numel()),
             "rhs_rel_l1": rhs_l1, "rhs_rel_linf": rhs_linf,
             "rhs_rel_l1_per_field": rhs_l1_field,
@@ -347,10 +415,20 @@ def run_ours(args, rank, world):
                    "(bench.fp64_flops_per_cell_rhs_mixed); FP32 and tensor-core work not counted")
         launches_per_step = 8
     achieved = fl / (rhs_avg * 1e-3) / 1e12
-    peak = fp64_peak_tflops()
-    # the FP64 and FP32 FMA rates measured on this GPU in the same run
+    # the FP64 and FP32 FMA rates measured on this GPU in the same run: the
+    # FP64 one is the roofline's peak
     meas64 = neno6.pipe_peak("fp64") / 1e12
     meas32 = neno6.pipe_peak("fp32") / 1e12
+    peak = meas64
+    tensor = None
+    if prec != "fp64":
+        # the classifier's multiply-adds (16 calls per cell and RHS) against
+        # the tensor cores' measured dense 16-bit rate
+        tfl = mlp_flops_per_cell_rhs() * cells
+        tpeak, tsrc = tensor_peak_tflops()
+        tach = tfl / (rhs_avg * 1e-3) / 1e12
+        tensor = {"achieved": round(tach, 2), "peak": tpeak, "unit": "TFLOP/s",
+                  "frac": round(tach / tpeak, 4), "flops_per_launch": tfl, "peak_source": tsrc}
     state_bytes = U.numel() * 8
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
@@ -363,18 +441,20 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2 (state %d MB)" % (state_bytes >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": kname, "flops_counted": fl_note,
-                     "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+                     "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": round(traffic_bytes(prec, n)),
+                     "traffic": traffic_bytes(prec, n),
                      "traffic_source": TRAFFIC_NOTE[prec == "fp64"],
-                     "peak_source": "FP64 pipe: 2 DFMA per clock per SM (ncu's sustained peak) "
-                                    "x 152 SMs x 2 flops x 2070 MHz",
+                     "peak_source": "measured in this run: DFMA chains on every SM (neno6_pipe_peak)",
+                     "nominal_fp64_tflops": fp64_peak_tflops(),
+                     "frac_of_nominal_fp64": round(achieved / fp64_peak_tflops(), 4),
                      "flops_per_launch": fl, "ms_per_launch": round(rhs_avg, 3),
-                     "fp64_fma_measured_tflops": round(meas64, 4),
-                     "frac_of_measured_fp64": round(achieved / meas64, 4),
-                     "fp32_fma_measured_tflops": round(meas32, 2)},
+                     "fp32_fma_measured_tflops": round(meas32, 2),
+                     "tensor": tensor},
         "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
-                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "steps": e2e_steps, "h2d_copy_gbs": round(h2d_gbs, 1),
+                "pinned_host_numa_node": numa[0] if numa else None},
         "gpu_launches": launches_per_step * args.steps,
         "vs_fp64_gpu": compare,
         "secondary": extra,
@@ -385,19 +465,19 @@ def run_ours(args, rank, world):
     return line
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the current kernels at 2048^2, scaled by cells
-# for other grids (the traffic is U once, the face fluxes once and the halo
-# re-reads, all proportional to the cells)
-TRAFFIC_2048 = {True: 141.2e6 + 96.6e6, False: 287.6e6 + 236.8e6}
-TRAFFIC_NOTE = {True: "rhs_fp64_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
-                      "capture at 2048^2, scaled by cells",
-                False: "faces_mixed_kernel, dram__bytes_read.sum + dram__bytes_write.sum of one ncu "
-                       "capture at 2048^2, scaled by cells"}
+# DRAM bytes (read + write) of one launch of the dominant kernel(s), from one
+# ncu capture of the current kernels at the grid named (dram__bytes_read.sum
+# + dram__bytes_write.sum, a single-pass capture); other grids: None
+TRAFFIC = {True: (2048, 141937152 + 94543104),
+           False: (4096, 1199868672 + 1050030336 + 1074064128 + 507846144)}
+TRAFFIC_NOTE = {True: "rhs_fp64_kernel at 2048^2, one launch: 141.9 MB read + 94.5 MB written",
+                False: "one RHS at 4096^2: faces_mixed_kernel 1199.9 MB read + 1050.0 MB written, "
+                       "diff_mixed_kernel 1074.1 MB read + 507.8 MB written"}
 
 
 def traffic_bytes(prec, n):
-    return TRAFFIC_2048[prec == "fp64"] * (n * n) / 2048.0 ** 2
+    grid, b = TRAFFIC[prec == "fp64"]
+    return b if (b is not None and grid == n) else None
 
 
 def max_over_ranks(values, world, device):
@@ -437,13 +517,19 @@ def fp64_peak_tflops():
 
 
 # ---------------------------------------------------------- oracle arm
-def oracle_timing(crop=64, reps=1):
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_timing(crop=64, reps=1, threads=1):
     """The FP64 CPU oracle on a periodic crop of the workload (same
-    generator, crop x crop cells): one SSP-RK3 step per rep."""
+    generator, crop x crop cells): one SSP-RK3 step per rep, on `threads`
+    host threads (OpenMP over the faces)."""
     import oracle
     import synth
     from oracle.weights import Net
     net = Net.load(WEIGHTS) if os.path.exists(WEIGHTS) else Net.random()
+    oracle.set_threads(threads)
     o = oracle.Oracle(ndim=2, nx=crop, ny=crop, net=net)
     U = synth.quadrants_2d(crop, crop)
     t0 = time.perf_counter()
@@ -453,29 +539,73 @@ def oracle_timing(crop=64, reps=1):
     return crop * crop * reps / dt / 1e6, dt
 
 
+def oracle_rhs_rate(n, threads):
+    """Cell-RHS evaluations per second (millions) of the FP64 oracle on the
+    n x n periodic quadrant workload: one full RHS on `threads` threads."""
+    import oracle
+    import synth
+    from oracle.weights import Net
+    net = Net.load(WEIGHTS) if os.path.exists(WEIGHTS) else Net.random()
+    got = oracle.set_threads(threads)
+    o = oracle.Oracle(ndim=2, nx=n, ny=n, net=net)
+    U = synth.quadrants_2d(n, n)
+    t0 = time.perf_counter()
+    o.rhs(U)
+    dt = time.perf_counter() - t0
+    return n * n / dt / 1e6, dt, got
+
+
+def cpu_baseline_line(args):
+    """The oracle on this host: all cores at each of --cpu-sizes, one core at
+    the smallest; the value is the all-core rate at the largest size, as
+    cell-updates (one update = three RHS)."""
+    cores = host_cores()
+    sizes = sorted(int(x) for x in args.cpu_sizes.split(",") if x)
+    per, total = {}, 0.0
+    for n in sizes:
+        r, secs, used = oracle_rhs_rate(n, cores)
+        per[str(n)] = {"all_cores_Mcell_rhs_per_s": round(r, 6), "threads": used, "seconds": round(secs, 2)}
+        total += secs
+    one = [n for n in sizes if n <= 1024] or sizes[:1]
+    for n in one:
+        r1, secs1, _ = oracle_rhs_rate(n, 1)
+        per[str(n)]["one_core_Mcell_rhs_per_s"] = round(r1, 6)
+        total += secs1
+    top = per[str(sizes[-1])]["all_cores_Mcell_rhs_per_s"]
+    return {"value": round(top / 3.0, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one FP64 oracle RHS of the %d^2 periodic quadrant workload on all %d host cores "
+                      "(OpenMP over faces), as cell-updates/s = cell-RHS/s / 3; also %s on all cores and "
+                      "%s on one core (%.1f s of wall time in all)" % (
+                          sizes[-1], cores, ", ".join("%d^2" % n for n in sizes[:-1]) or "no other size",
+                          ", ".join("%d^2" % n for n in one), total),
+            "per_size": per}
+
+
 def workload_name(n, prec):
     return "2D Euler %dx%d periodic, %s NENO6 RHS, SSP-RK3 (CFL 0.4)" % (
         n, n, "FP64" if prec == "fp64" else "mixed-precision (%s classifier)" % prec)
 
 
 def run_reference(args):
-    oracle_timing(16, 1)  # build + warm the oracle library
+    cores = host_cores()
+    oracle_timing(16, 1, cores)  # build + warm the oracle library
     for _ in range(args.warmup):
-        oracle_timing(args.ref_crop, 1)
+        oracle_timing(args.ref_crop, 1, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_timing(args.ref_crop, 1)
+        oracle_timing(args.ref_crop, 1, cores)
     dt = time.perf_counter() - t0
     value = args.ref_crop ** 2 * args.steps / dt / 1e6
     sample = ("one FP64 SSP-RK3 step of the oracle on a %dx%d periodic crop of the %d^2 "
-              "workload per step" % (args.ref_crop, args.ref_crop, args.n))
+              "workload per step, %d host threads (OpenMP over faces)" % (
+                  args.ref_crop, args.ref_crop, args.n, cores))
     return {
         "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 1, "impl": "reference",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_name(args.n, args.precision),
                                         "sample": sample},
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -609,8 +739,8 @@ def main():
     ap.add_argument("--vjp-only", action="store_true")
     ap.add_argument("--classify-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
-    ap.add_argument("--ref-crop", type=int, default=48)
-    ap.add_argument("--cpu-crop", type=int, default=384)
+    ap.add_argument("--ref-crop", type=int, default=192)
+    ap.add_argument("--cpu-sizes", default="256,1024,2048")
     ap.add_argument("--workload", choices=["quadrants", "oblique"], default="quadrants")
     args = ap.parse_args()
     if args.workload == "oblique" and args.impl == "ours":
@@ -637,11 +767,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     line = run_ours(args, rank, world)
     if rank == 0:
-        v, secs = oracle_timing(args.cpu_crop, 1)
-        line["cpu_baseline"] = {
-            "value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one SSP-RK3 step (3 RHS) of a %dx%d periodic crop of the workload, "
-                      "%.1f s of CPU time" % (args.cpu_crop, args.cpu_crop, secs)}
+        line["cpu_baseline"] = cpu_baseline_line(args)
         print(json.dumps(line))
     if world > 1:
         import torch

@@ -50,6 +50,9 @@
 // classifier mask and the alpha argmax frozen, which the tests use to check the
 // CUDA adjoint by the dot-product identity <lambda, J v> = <J^T lambda, v>.
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -536,6 +539,10 @@ int rhs_impl(const OracleParams& P, const T* U, T* dUdt, const uint8_t* mask_in,
   int bad = 0;
   std::vector<T> Fx((size_t)ny * (nx + 1) * nv);
   std::vector<T> Fy(P.ndim == 2 ? (size_t)(ny + 1) * nx * nv : 0);
+  // Faces are independent: with OpenMP the lines of faces are shared among
+  // threads; every face's arithmetic, and where its result goes, is the
+  // same as in a serial run.
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
   for (int j = 0; j < ny; ++j)
     for (int f = 0; f <= nx; ++f) {
       uint8_t eta[4] = {0, 0, 0, 0};
@@ -545,7 +552,8 @@ int rhs_impl(const OracleParams& P, const T* U, T* dUdt, const uint8_t* mask_in,
       if (mask_out)
         for (int m = 0; m < nv; ++m) mask_out[mask_x_index(P, m, j, f)] = eta[m];
     }
-  if (P.ndim == 2)
+  if (P.ndim == 2) {
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
     for (int f = 0; f <= ny; ++f)
       for (int i = 0; i < nx; ++i) {
         uint8_t eta[4] = {0, 0, 0, 0};
@@ -555,7 +563,9 @@ int rhs_impl(const OracleParams& P, const T* U, T* dUdt, const uint8_t* mask_in,
         if (mask_out)
           for (int m = 0; m < nv; ++m) mask_out[mask_y_index(P, m, f, i)] = eta[m];
       }
+  }
   size_t plane = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i)
       for (int n = 0; n < nv; ++n) {
@@ -575,6 +585,18 @@ int rhs_impl(const OracleParams& P, const T* U, T* dUdt, const uint8_t* mask_in,
 }  // namespace
 
 extern "C" {
+
+// Threads of the face loops (OpenMP builds; 1 otherwise): sets the count for
+// later calls (n >= 1) and returns the count in force.
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 // dU/dt of the whole grid.  U, dUdt: [nv][ny][nx] FP64.  mask_in is read when
 // mask_mode == 3; mask_out (nullable) receives the classifier bits, layout
