@@ -87,6 +87,14 @@ def mlp_flops_per_cell_rhs(ndim=2):
     return 2 * nv * ndim * 2 * (6 * 64 + 64 * 32 + 32 * 16 + 16 * 8 + 8 * 4)
 
 
+def mlp_grad_flops_per_sample():
+    """Algorithmic flops of one sample's loss gradient: the forward pass
+    (3104 multiply-adds), the deltas of layers 4..1 (4x8 + 8x16 + 16x32 + 32x64
+    multiply-adds) and the weight gradients (3104 multiply-adds)."""
+    fwd = 6 * 64 + 64 * 32 + 32 * 16 + 16 * 8 + 8 * 4
+    return 2 * (fwd + (4 * 8 + 8 * 16 + 16 * 32 + 32 * 64) + fwd)
+
+
 def tensor_peak_tflops():
     """Dense 16-bit tensor-core rate (fp16 and bf16 run at the same rate):
     the sustained cuBLAS figure of MEASURED_PEAKS.json (the kernel runs inside
@@ -348,7 +356,26 @@ def run_ours(args, rank, world):
             g64.mlp_bwd(Xs, ys)
         e_b.record(stream)
         torch.cuda.synchronize()
-        extra["mlp_bwd_2^20"] = {"ms_per_call": round(e_a.elapsed_time(e_b) / 3, 3)}
+        extra["mlp_bwd_2^20"] = {"ms_per_call": round(e_a.elapsed_time(e_b) / 3, 3),
+                                 "arithmetic": "FP32, CUDA cores (FP64 handle)"}
+        # the same gradient on the tensor cores (fp16 handle)
+        g16 = neno6.Neno6(ndim=1, nx=8, precision="fp16", weights=weights)
+        g16.mlp_bwd(Xs, ys)
+        e_a.record(stream)
+        for _ in range(3):
+            g16.mlp_bwd(Xs, ys)
+        e_b.record(stream)
+        torch.cuda.synchronize()
+        tc_ms = e_a.elapsed_time(e_b) / 3
+        tfl = (1 << 20) * mlp_grad_flops_per_sample()
+        tpeak, tsrc = tensor_peak_tflops()
+        extra["mlp_bwd_tc_2^20"] = {
+            "ms_per_call": round(tc_ms, 3), "arithmetic": "fp16 operands, FP32 accumulation, tcgen05",
+            "speedup_vs_fp32": round(extra["mlp_bwd_2^20"]["ms_per_call"] / tc_ms, 2),
+            "tensor": {"achieved": round(tfl / (tc_ms * 1e-3) / 1e12, 2), "peak": tpeak, "unit": "TFLOP/s",
+                       "frac": round(tfl / (tc_ms * 1e-3) / 1e12 / tpeak, 4),
+                       "flops_per_call": tfl, "peak_source": tsrc}}
+        g16.close()
         # the 709 000 samples of Algorithm 1 / Table 9 generated on the GPU
         # from seeded uniform draws, then one training epoch of the Table 2
         # recipe on their 70 % training share: 496 300 samples, batch 175, Adam

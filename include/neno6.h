@@ -219,9 +219,11 @@ int neno6_rhs_vjp(neno6_handle* h, const double* U, const double* lambda, const 
  * neno6_mlp_bwd — gradient of the classifier's training loss for retraining:
  * the mean binary cross entropy of Eq. (Crossentropy) (mean over the n
  * samples and the S = 4 outputs, sigmoid outputs of Sec. 3.1) with respect
- * to every parameter of the handle's network, in FP32; the stencils are
- * normalised as in Eq. (normalizainput) first.  Deterministic (fixed-order
- * reductions).
+ * to every parameter of the handle's network; the stencils are normalised as
+ * in Eq. (normalizainput) first.  Deterministic (fixed-order reductions).
+ * An FP64 handle computes it in FP32 on the CUDA cores; a mixed-precision
+ * handle on the tensor cores (its bf16 / fp16 operands: the network's
+ * weights, activations and deltas rounded to 16 bits, FP32 accumulation).
  *   X        [n][6] float64 stencil values.
  *   labels   [n] uint8, bit k = eta_k (1: stencil S_k discarded).
  *   n        1 <= n < 2^31.

@@ -31,6 +31,7 @@ SOURCES = {
     "mixed_rhs.cu": [],
     "vjp.cu": ["-fmad=false"],
     "mlp_bwd.cu": [],
+    "mlp_bwd_tc.cu": [],
     "mlp_train.cu": [],
     "scalar.cu": ["-fmad=false"],
     "datagen.cu": ["-fmad=false"],

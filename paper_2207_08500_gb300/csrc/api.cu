@@ -32,6 +32,7 @@ struct neno6_handle {
   double* d_stage = nullptr;  // two RK3 stage states (lazily allocated)
   double* d_host_state = nullptr;  // device copy of neno6_step_host's state (lazily)
   uint8_t* d_net_image = nullptr;  // tensor-core classifier image (mixed precision)
+  uint8_t* d_bwd_image = nullptr;  // its backward image (tensor-core gradient)
   float* d_guard_w = nullptr;      // FP32 transposed parameters (guard band)
   double* d_faces = nullptr;       // x- and y-face fluxes (mixed precision, lazily)
   uint8_t* d_mask = nullptr;       // classifier mask of the adjoint's forward pass (lazily)
@@ -429,6 +430,13 @@ int neno6_create(const neno6_config* cfg, const char* weights_path, neno6_handle
       build_net_image(h->net, c.precision == NENO6_MIXED_BF16, img.data());
     e = cudaMalloc(&h->d_net_image, kNetImageBytes);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_net_image, img.data(), kNetImageBytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !h->narrow) {
+      std::vector<uint8_t> bimg(kBwdImageBytes);
+      build_bwd_image(h->net, c.precision == NENO6_MIXED_BF16, bimg.data());
+      e = cudaMalloc(&h->d_bwd_image, kBwdImageBytes);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(h->d_bwd_image, bimg.data(), kBwdImageBytes, cudaMemcpyHostToDevice);
+    }
     std::vector<float> gimg(kNetParams);
     build_guard_image(h->net, gimg.data());
     if (e == cudaSuccess) e = cudaMalloc(&h->d_guard_w, kNetParams * sizeof(float));
@@ -457,6 +465,7 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_stage);
   cudaFree(h->d_host_state);
   cudaFree(h->d_net_image);
+  cudaFree(h->d_bwd_image);
   cudaFree(h->d_guard_w);
   cudaFree(h->d_faces);
   cudaFree(h->d_guard_count);
@@ -690,7 +699,11 @@ int neno6_mlp_bwd(neno6_handle* h, const double* X, const uint8_t* labels, int64
       return cuda_fail(h, e, "mlp_bwd: scratch");
     }
   }
-  cudaError_t e = launch_mlp_bwd(X, labels, n, h->d_params32, grad, loss, h->d_bwd_scratch, (cudaStream_t)stream);
+  cudaError_t e =
+      h->cfg.precision == NENO6_FP64
+          ? launch_mlp_bwd(X, labels, n, h->d_params32, grad, loss, h->d_bwd_scratch, (cudaStream_t)stream)
+          : launch_mlp_bwd_tc(X, labels, n, h->d_net_image, h->d_bwd_image, h->cfg.precision == NENO6_MIXED_BF16,
+                              grad, loss, h->d_bwd_scratch, h->d_status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "mlp_bwd launch");
   return NENO6_OK;
 }

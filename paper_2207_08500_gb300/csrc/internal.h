@@ -115,6 +115,18 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img);
 // FP32 parameters with every W transposed to [in][out] (guard re-evaluation).
 void build_guard_image(const NetF64& net, float* img);
 
+// Backward image of the classifier for the tensor-core gradient kernel: the
+// transposed weights of layers 3 and 2 as 16-bit B operands (K-major, N x K
+// = W3^T [32][16] and W2^T [64][32]), then W4 [8][16] and W5 [4][8] in FP32
+// for the CUDA-core part of the backward pass.
+constexpr int kBwdBW3 = 0;
+constexpr int kBwdBW2 = kBwdBW3 + 32 * 16 * 2;
+constexpr int kBwdW4 = kBwdBW2 + 64 * 32 * 2;
+constexpr int kBwdW5 = kBwdW4 + 8 * 16 * 4;
+constexpr int kBwdImageBytes = kBwdW5 + 4 * 8 * 4;
+static_assert(kBwdImageBytes % 128 == 0, "backward image is copied in 16-byte chunks, 128-byte aligned");
+void build_bwd_image(const NetF64& net, bool bf16, uint8_t* img);
+
 // Linear weights d_k (printed optimal weights, or the sixth-order test
 // weights), candidate coefficients of S0..S3 and the renormalised weights of
 // every mask pattern: the tables every FP64 launch parameter block carries.
@@ -175,6 +187,14 @@ int mlp_bwd_blocks(long long n);
 size_t mlp_bwd_scratch_bytes(long long n);
 cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const float* params, float* grad,
                            float* loss, void* scratch, cudaStream_t s);
+// The same gradient on the tensor cores (mixed-precision handles): 16-bit
+// operands, FP32 accumulation; scratch of mlp_bwd_scratch_bytes(n) bytes.
+cudaError_t launch_mlp_bwd_tc(const double* X, const uint8_t* y, long long n, const uint8_t* net_image,
+                              const uint8_t* bwd_image, bool bf16, float* grad, float* loss, void* scratch,
+                              int* status, cudaStream_t s);
+// grad[p] = scale * (sum over the partial sums of the CTAs, in CTA order)
+cudaError_t launch_mlp_bwd_reduce(const float* partial, const double* partial_loss, int blocks, long long n,
+                                  float scale, float* grad, float* loss, cudaStream_t s);
 // Scalar conservation laws (1D): law 0 linear advection, 1 Burgers.
 struct ScalarParams {
   RhsArgs a;        // grid, boundary, mask mode, candidates, weights

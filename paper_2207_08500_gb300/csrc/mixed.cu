@@ -182,6 +182,24 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
   }
 }
 
+// Host: the backward image (kBwd* layout).
+void build_bwd_image(const NetF64& net, bool bf16, uint8_t* img) {
+  std::memset(img, 0, kBwdImageBytes);
+  auto put = [&](int off, int K, int n, int k, double w) {
+    const uint16_t b = bf16 ? to_bf16_bits(w) : to_fp16_bits(w);
+    std::memcpy(img + off + kmajor_offset(n, k, K), &b, 2);
+  };
+  // W3 [16 out][32 in] at 2528, W2 [32][64] at 448: B[n = in][k = out]
+  for (int o = 0; o < 16; ++o)
+    for (int i = 0; i < 32; ++i) put(kBwdBW3, 16, i, o, net.p[2528 + o * 32 + i]);
+  for (int o = 0; o < 32; ++o)
+    for (int i = 0; i < 64; ++i) put(kBwdBW2, 32, i, o, net.p[448 + o * 64 + i]);
+  float* w4 = reinterpret_cast<float*>(img + kBwdW4);
+  float* w5 = reinterpret_cast<float*>(img + kBwdW5);
+  for (int q = 0; q < 8 * 16; ++q) w4[q] = (float)net.p[3056 + q];
+  for (int q = 0; q < 4 * 8; ++q) w5[q] = (float)net.p[3192 + q];
+}
+
 // Host: the tensor-core image of the 6-32-32-32-4 network (kNarrow* layout).
 void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
   std::memset(img, 0, kNetImageBytes);

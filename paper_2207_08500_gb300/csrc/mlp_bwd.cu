@@ -72,14 +72,16 @@ __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ 
   if (t == 0) partial_loss[blockIdx.x] = sl[0];
 }
 
-// grad[p] = sum_b partial[b][p] in block order; loss likewise (deterministic).
+// grad[p] = scale * sum_b partial[b][p] in block order; loss likewise
+// (deterministic).  scale is 1 for partial sums of deltas that carry the
+// 1/(n S) of the mean, 1/(n S) for sums of unscaled deltas.
 __global__ void mlp_bwd_reduce_kernel(const float* __restrict__ partial, const double* __restrict__ partial_loss,
-                                      int blocks, long long n, float* __restrict__ grad, float* loss) {
+                                      int blocks, long long n, float scale, float* __restrict__ grad, float* loss) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < kNetParams) {
     float a = 0.0f;
     for (int b = 0; b < blocks; ++b) a += partial[(size_t)b * kNetParams + p];
-    grad[p] = a;
+    grad[p] = a * scale;
   }
   if (p == 0 && loss) {
     double l = 0.0;
@@ -95,9 +97,11 @@ int mlp_bwd_blocks(long long n) {
   return (int)(tiles < 152 ? tiles : 152);
 }
 
+// Partial sums of up to 2 x 152 CTAs (the tensor-core kernel runs two per SM).
 size_t mlp_bwd_scratch_bytes(long long n) {
-  const int b = mlp_bwd_blocks(n);
-  return (size_t)b * kNetParams * sizeof(float) + (size_t)b * sizeof(double);
+  const long long tiles = (n + kT - 1) / kT;
+  const size_t b = (size_t)(tiles < 2 * 152 ? tiles : 2 * 152);
+  return b * kNetParams * sizeof(float) + b * sizeof(double);
 }
 
 cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const float* params, float* grad,
@@ -112,7 +116,13 @@ cudaError_t launch_mlp_bwd(const double* X, const uint8_t* y, long long n, const
   mlp_bwd_kernel<<<blocks, kT, smem, s>>>(X, y, n, params, partial, partial_loss);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  mlp_bwd_reduce_kernel<<<(kNetParams + 255) / 256, 256, 0, s>>>(partial, partial_loss, blocks, n, grad, loss);
+  return launch_mlp_bwd_reduce(partial, partial_loss, blocks, n, 1.0f, grad, loss, s);
+}
+
+cudaError_t launch_mlp_bwd_reduce(const float* partial, const double* partial_loss, int blocks, long long n,
+                                  float scale, float* grad, float* loss, cudaStream_t s) {
+  mlp_bwd_reduce_kernel<<<(kNetParams + 255) / 256, 256, 0, s>>>(partial, partial_loss, blocks, n, scale, grad,
+                                                                 loss);
   return cudaGetLastError();
 }
 
