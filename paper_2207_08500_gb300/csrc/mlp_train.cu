@@ -4,14 +4,12 @@
 // order of a caller-given permutation of the samples.
 //
 // Mini-batch Adam is sequential (every step reads the parameters the
-// previous step wrote), so one persistent CTA of 192 threads runs all the
-// steps of a call: per step one thread per sample runs the forward and
-// backward pass (mlp_fb.cuh) against the parameters in shared memory, then
-// each thread sums the batch gradient of the ~17 parameters it owns and
-// applies the Adam update to them, keeping their moments in registers.  No
-// launch per step and no global-memory round trip of the parameters; each
-// thread accumulates its samples' share of the loss and the shares are
-// reduced in a fixed order at the end, so a call is deterministic.
+// previous step wrote), so one persistent cluster of CTAs runs all the steps
+// of a call, sharing each step's batch (below).  One thread per sample runs
+// the forward and backward pass (mlp_fb.cuh) against the parameters in
+// shared memory.  No launch per step and no global-memory round trip of the
+// parameters; the gradient and the loss are reduced in a fixed order, so a
+// call is deterministic.
 #include "internal.h"
 #include "mlp_fb.cuh"
 
@@ -20,103 +18,183 @@ namespace {
 
 using namespace mlpfb;
 
-constexpr int kB = kMaxTrainBatch;      // threads = largest batch
-constexpr int kPitch = kB + 1;          // feature-major rows, padded
-constexpr int kPer = (kNetParams + kB - 1) / kB;  // parameters owned per thread
-constexpr int kSmemFloats = kNetParams + kRows * kPitch;
-constexpr int kRed = 256;  // loss reduction width (power of two >= kB)
-static_assert(kSmemFloats * 4 + kRed * 8 <= 227 * 1024, "training kernel shared memory");
+// The training loop on a cluster of kCl CTAs (kCl SMs): every step's
+// batch is shared among the CTAs (at most kPerCta samples each).  Each CTA
+// runs its samples' forward and backward passes and forms the partial
+// gradient of all 3228 parameters over them; after a cluster barrier, CTA r
+// sums the partials of the parameter slice it owns over the kCl CTAs (read
+// from their shared memory, in rank order: deterministic), applies Adam to
+// that slice (its moments stay in its shared memory for the whole call) and
+// publishes the new values; after a second barrier every CTA gathers the
+// slices into its copy of the parameters.
+constexpr int kCl = 8;
+constexpr int kCT = 128;                                    // threads per CTA
+constexpr int kPerCta = (kMaxTrainBatch + kCl - 1) / kCl;    // samples per CTA (24)
+constexpr int kCPitch = kPerCta + 1;
+constexpr int kSlice = (kNetParams + kCl - 1) / kCl;         // 404 parameters per CTA
+constexpr int kCPer = (kNetParams + kCT - 1) / kCT;          // partial sums per thread
+// floats: W, staging, partial gradient, published slice, Adam m and v
+constexpr int kCOffW = 0, kCOffSt = kNetParams, kCOffPart = kCOffSt + kRows * kCPitch;
+constexpr int kCOffSlice = kCOffPart + kNetParams, kCOffM = kCOffSlice + kSlice, kCOffV = kCOffM + kSlice;
+constexpr int kCSmemFloats = kCOffV + kSlice;
+static_assert(kPerCta <= 32 && kSlice <= 4 * kCT, "one warp of samples, four slice entries per thread");
 
-__global__ void __launch_bounds__(kB, 1) mlp_train_kernel(const MlpTrainArgs a) {
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// float at shared-memory pointer p of the cluster's CTA `rank`
+__device__ __forceinline__ float ld_cluster(const float* p, uint32_t rank) {
+  uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(p)), remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kCT, 1) mlp_train_cluster_kernel(const MlpTrainArgs a) {
   extern __shared__ float sm[];
-  float* W = sm;
-  float* st = sm + kNetParams;
-  __shared__ double sl[kRed];
+  float* W = sm + kCOffW;
+  float* st = sm + kCOffSt;
+  float* part = sm + kCOffPart;
+  float* slice = sm + kCOffSlice;
+  float* mm = sm + kCOffM;
+  float* vv = sm + kCOffV;
+  __shared__ double sl[kCT];
   const int t = threadIdx.x;
-  for (int i = t; i < kNetParams; i += kB) W[i] = a.params[i];
-  float mq[kPer], vq[kPer];
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int p = t + q * kB;
-    mq[q] = p < kNetParams ? a.m[p] : 0.0f;
-    vq[q] = p < kNetParams ? a.v[p] : 0.0f;
+  const uint32_t rank = cluster_rank();
+  const int p_lo = (int)rank * kSlice;
+  for (int i = t; i < kNetParams; i += kCT) W[i] = a.params[i];
+  for (int i = t; i < kSlice; i += kCT) {
+    const int p = p_lo + i;
+    mm[i] = p < kNetParams ? a.m[p] : 0.0f;
+    vv[i] = p < kNetParams ? a.v[p] : 0.0f;
   }
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float lr = a.lr;
-  double loss_sum = 0.0;  // this thread's samples' share of sum_steps (batch-mean BCE)
+  double loss_sum = 0.0;
   bool bad_index = false;
-  // beta^t of the step before this call's first (bias corrections)
   double p1 = pow(0.9, (double)a.t0), p2 = pow(0.999, (double)a.t0);
   __syncthreads();
   const long long steps = (a.n_perm + a.batch - 1) / a.batch;
   for (long long step = 0; step < steps; ++step) {
     const long long s0 = step * a.batch;
     const int nb = (int)min((long long)a.batch, a.n_perm - s0);
-    bool live = t < nb;
-    long long idx = 0;
-    if (live) {
-      idx = a.perm[s0 + t];
-      if (idx < 0 || idx >= a.n) {  // out-of-range sample: skipped, reported
-        bad_index = true;
-        live = false;
-        idx = 0;
+    const int per = (nb + kCl - 1) / kCl;
+    const int first = min((int)rank * per, nb), ns = min(per, nb - first);
+    // ---- this CTA's samples: forward and backward (one thread each)
+    if (t < 32) {
+      bool live = t < ns;
+      long long idx = 0;
+      if (live) {
+        idx = a.perm[s0 + first + t];
+        if (idx < 0 || idx >= a.n) {
+          bad_index = true;
+          live = false;
+          idx = 0;
+        }
+      }
+      if (t < kPerCta) {
+        float xr[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) xr[j] = live ? (float)a.X[idx * 6 + j] : 0.0f;
+        double loss = 0.0;
+        sample_fwd_bwd<kCPitch>(W, st, t, live, xr, live ? a.y[idx] : 0u, 1.0f / (4.0f * (float)nb), loss);
+        loss_sum += loss * (0.25 / (double)nb);
       }
     }
-    float xr[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) xr[j] = live ? (float)a.X[idx * 6 + j] : 0.0f;
-    double loss = 0.0;
-    sample_fwd_bwd<kPitch>(W, st, t, live, xr, live ? a.y[idx] : 0u, 1.0f / (4.0f * (float)nb), loss);
-    loss_sum += loss * (0.25 / (double)nb);
     __syncthreads();
-    // Adam (Kingma & Ba, Algorithm 1) on the owned parameters; the step count
-    // runs on across calls (t0 steps before this one)
+    // ---- partial gradient of every parameter over these samples
+#pragma unroll 1
+    for (int q = 0; q < kCPer; ++q) {
+      const int p = t + q * kCT;
+      if (p < kNetParams) part[p] = param_grad<kCPitch>(st, p, ns);
+    }
+    cluster_sync();
+    // ---- this CTA's slice: sum over the CTAs (rank order), Adam, publish
     p1 *= 0.9;
     p2 *= 0.999;
-    const float c1 = (float)(1.0 / (1.0 - p1));  // 1 / (1 - beta1^t)
-    const float c2 = (float)(1.0 / (1.0 - p2));  // 1 / (1 - beta2^t)
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int p = t + q * kB;
+    const float c1 = (float)(1.0 / (1.0 - p1));
+    const float c2 = (float)(1.0 / (1.0 - p2));
+    for (int i = t; i < kSlice; i += kCT) {
+      const int p = p_lo + i;
       if (p < kNetParams) {
-        const float g = param_grad<kPitch>(st, p, nb);
-        mq[q] = fmaf(b1, mq[q], (1.0f - b1) * g);
-        vq[q] = fmaf(b2, vq[q], (1.0f - b2) * (g * g));
-        const float mh = mq[q] * c1, vh = vq[q] * c2;
-        W[p] -= lr * mh / (sqrtf(vh) + eps);
+        float g = 0.0f;
+#pragma unroll
+        for (int r = 0; r < kCl; ++r) g += ld_cluster(part + p, (uint32_t)r);
+        mm[i] = fmaf(b1, mm[i], (1.0f - b1) * g);
+        vv[i] = fmaf(b2, vv[i], (1.0f - b2) * (g * g));
+        const float mh = mm[i] * c1, vh = vv[i] * c2;
+        slice[i] = W[p] - lr * mh / (sqrtf(vh) + eps);
       }
+    }
+    cluster_sync();
+    // ---- every CTA gathers the new parameters
+    for (int p = t; p < kNetParams; p += kCT) {
+      const int owner = p / kSlice;
+      W[p] = ld_cluster(slice + (p - owner * kSlice), (uint32_t)owner);
     }
     __syncthreads();
   }
-  for (int i = t; i < kNetParams; i += kB) a.params[i] = W[i];
-#pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    const int p = t + q * kB;
+  // results: every CTA holds the parameters; each writes its own slice and
+  // moments
+  for (int i = t; i < kSlice; i += kCT) {
+    const int p = p_lo + i;
     if (p < kNetParams) {
-      a.m[p] = mq[q];
-      a.v[p] = vq[q];
+      a.params[p] = W[p];
+      a.m[p] = mm[i];
+      a.v[p] = vv[i];
     }
   }
-  // sum of the per-step batch-mean losses: fixed-order tree over the threads
+  // loss: per CTA a fixed-order tree, then the CTAs in rank order
   sl[t] = loss_sum;
-  if (t < kRed - kB) sl[kB + t] = 0.0;
   __syncthreads();
-  for (int w = kRed / 2; w > 0; w >>= 1) {
+  for (int w = kCT / 2; w > 0; w >>= 1) {
     if (t < w) sl[t] += sl[t + w];
     __syncthreads();
   }
-  if (t == 0 && a.loss_sum) *a.loss_sum = sl[0];
+  float* lossf = part;  // the CTA's loss as two floats (hi, lo) for the gather
+  if (t == 0) {
+    const double v = sl[0];
+    lossf[0] = (float)v;
+    lossf[1] = (float)(v - (double)(float)v);
+  }
+  cluster_sync();
+  if (rank == 0 && t == 0 && a.loss_sum) {
+    double tot = 0.0;
+    for (int r = 0; r < kCl; ++r) tot += (double)ld_cluster(lossf, (uint32_t)r) + (double)ld_cluster(lossf + 1, (uint32_t)r);
+    *a.loss_sum = tot;
+  }
   if (bad_index) atomicOr(a.status, 8);
+  cluster_sync();  // no CTA leaves while another may still read its memory
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_train(const MlpTrainArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)kSmemFloats * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one cluster of kCl CTAs
+  const size_t smem = (size_t)kCSmemFloats * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(mlp_train_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  mlp_train_kernel<<<1, kB, smem, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCl, 1, 1);
+  cfg.blockDim = dim3(kCT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, mlp_train_cluster_kernel, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace neno6
