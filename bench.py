@@ -484,12 +484,23 @@ def run_ours(args, rank, world):
                 "pinned_host_numa_node": numa[0] if numa else None},
         "gpu_launches": launches_per_step * args.steps,
         "vs_fp64_gpu": compare,
+        "precision_note": PRECISION_NOTE.get(prec),
         "secondary": extra,
         "clocks": clock_info,
         "device_status": status,
         "weights_sha256": weights_sha256(weights),
     }
     return line
+
+
+# What the 100-step accuracy runs (2048^2, against the FP64 path) showed for
+# each classifier precision.
+PRECISION_NOTE = {
+    "fp16": "fp16 (guard tau 0.5) stays within 1e-6 relative L1 of the FP64 state over the 99-step 2048^2 run "
+            "(5.6e-7); bf16 does not (1.5e-5 at tau 1.0, 4.9e-6 at tau 4.0)",
+    "bf16": "bf16 does not stay within 1e-6 relative L1 of the FP64 state over the 99-step 2048^2 run "
+            "(1.5e-5 at tau 1.0, 4.9e-6 at tau 4.0); only fp16 does (5.6e-7)",
+}
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel(s), from one
