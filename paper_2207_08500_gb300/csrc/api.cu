@@ -41,6 +41,9 @@ struct neno6_handle {
   float* d_params32 = nullptr;     // FP32 parameters, weights-file order
   void* d_bwd_scratch = nullptr;   // per-CTA partial gradients (lazily)
   unsigned long long* d_guard_count = nullptr;
+  cudaStream_t copy_stream = nullptr;  // neno6_step_host: band copies in and out (lazily)
+  cudaEvent_t band_in[9] = {};         // band copied in; [8]: the step's stream reached the call
+  cudaEvent_t band_done[9] = {};       // band of the last stage done; [8]: all copied out
   FacesMixedArgs faces_args;
   size_t state_elems = 0;
   RhsParamsF64 rhs_params;        // launch parameter blocks (copied at launch)
@@ -317,12 +320,18 @@ int ensure_faces(neno6_handle* h) {
   return NENO6_OK;
 }
 
-// One mixed-precision RHS evaluation of U; stage 0 writes dU/dt to out,
-// stages 1..3 the RK3 stage state (dt from h->d_dt).
-int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, int stage, uint8_t* mask_out,
-              double* t_dev, cudaStream_t s) {
-  int rc = ensure_faces(h);
-  if (rc != NENO6_OK) return rc;
+int ensure_stage(neno6_handle* h) {
+  if (h->d_stage) return NENO6_OK;
+  cudaError_t e = cudaMalloc(&h->d_stage, 2 * h->state_elems * sizeof(double));
+  if (e != cudaSuccess) {
+    h->d_stage = nullptr;
+    return cuda_fail(h, e, "step: stage buffers");
+  }
+  return NENO6_OK;
+}
+
+// Face-kernel arguments of a mixed-precision RHS evaluation of U.
+void fill_faces_args(neno6_handle* h, const double* U, uint8_t* mask_out) {
   FacesMixedArgs& a = h->faces_args;
   std::memset(&a, 0, sizeof a);
   a.U = U;
@@ -346,11 +355,14 @@ int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, i
     for (int l = 0; l < 4; ++l) a.cand[k][l] = (float)h->cand[k][l];
   for (int e = 0; e < 16; ++e)
     for (int k = 0; k < 4; ++k) a.wtab[e][k] = (float)h->wtab[e][k];
-  cudaError_t e = launch_faces_mixed(h->cfg.ndim, a, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "mixed face kernel");
+}
+
+// Difference-kernel arguments for the rows j0 .. j1 - 1.
+DiffArgs diff_args(const neno6_handle* h, const double* U, const double* U0, double* out, int stage,
+                   double* t_dev, int j0, int j1) {
   DiffArgs d;
-  d.Fx = a.Fx;
-  d.Fy = a.Fy;
+  d.Fx = h->faces_args.Fx;
+  d.Fy = h->faces_args.Fy;
   d.U = U;
   d.U0 = U0;
   d.out = out;
@@ -361,12 +373,132 @@ int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, i
   d.stage = stage;
   d.bcx = h->cfg.bc[0];
   d.bcy = h->cfg.bc[1];
+  d.j0 = j0;
+  d.j1 = j1;
   d.inv_dx = 1.0 / h->cfg.dx;
   d.inv_dy = 1.0 / h->cfg.dy;
   d.third = 1.0 / 3.0;
   d.two_thirds = 2.0 / 3.0;
-  e = launch_diff_mixed(h->cfg.ndim, d, s);
+  return d;
+}
+
+// One mixed-precision RHS evaluation of U; stage 0 writes dU/dt to out,
+// stages 1..3 the RK3 stage state (dt from h->d_dt).
+int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, int stage, uint8_t* mask_out,
+              double* t_dev, cudaStream_t s) {
+  int rc = ensure_faces(h);
+  if (rc != NENO6_OK) return rc;
+  fill_faces_args(h, U, mask_out);
+  cudaError_t e = launch_faces_mixed(h->cfg.ndim, h->faces_args, s, 0, h->cfg.ny);
+  if (e != cudaSuccess) return cuda_fail(h, e, "mixed face kernel");
+  e = launch_diff_mixed(h->cfg.ndim, diff_args(h, U, U0, out, stage, t_dev, 0, h->cfg.ny), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "mixed difference kernel");
+  return NENO6_OK;
+}
+
+// Row bands of a host-state step on the mixed path: multiples of 16 rows,
+// at most eight (one band for 1D grids and grids under 512 rows).
+int band_rows(const neno6_handle* h) {
+  const int ny = h->cfg.ny;
+  int rows = (ny + 7) / 8;
+  rows = (rows + 15) / 16 * 16;
+  return (rows < 64 || h->cfg.ndim == 1) ? ny : rows;
+}
+
+int ensure_copy_stream(neno6_handle* h) {
+  if (h->copy_stream) return NENO6_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  for (int b = 0; b < 9 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&h->band_in[b], cudaEventDisableTiming);
+  for (int b = 0; b < 9 && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&h->band_done[b], cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host: copy stream");
+  return NENO6_OK;
+}
+
+// Copy rows r0 .. r1 - 1 of every field between a host state and a device
+// state (both [nv][ny][nx]).
+cudaError_t copy_rows(const neno6_handle* h, double* dst, const double* src, int r0, int r1, cudaMemcpyKind kind,
+                      cudaStream_t s) {
+  const size_t plane = (size_t)h->cfg.nx * h->cfg.ny;
+  cudaError_t e = cudaSuccess;
+  for (int n = 0; n < h->nv && e == cudaSuccess; ++n) {
+    const size_t off = n * plane + (size_t)r0 * h->cfg.nx;
+    e = cudaMemcpyAsync(dst + off, src + off, (size_t)(r1 - r0) * h->cfg.nx * sizeof(double), kind, s);
+  }
+  return e;
+}
+
+// Mixed-precision SSP-RK3 step of U (CFL reduction, dt, three stages).
+// With in_host / out_host (neno6_step_host), U is filled from in_host and
+// copied to out_host in row bands on the handle's copy stream, overlapped
+// with compute: the first stage's face fluxes (which do not depend on dt)
+// and the wave-speed maxima of each band start as soon as the band and its
+// neighbours have arrived, only the first stage's difference waits for dt;
+// the last stage runs band by band (face kernel of band b + 1, then the
+// difference of band b, whose top row needs the first y faces of band b + 1),
+// each band copied out as it finishes.  The arithmetic of every face and
+// cell, and dt (a maximum), are those of the unbanded step.  Stream s waits
+// for the copies before this returns.
+int mixed_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_dev, double* dt_dev,
+               const double* in_host, double* out_host, cudaStream_t s) {
+  int rc = ensure_faces(h);
+  if (rc == NENO6_OK && (in_host || out_host)) rc = ensure_copy_stream(h);
+  if (rc != NENO6_OK) return rc;
+  const int ndim = h->cfg.ndim, nx = h->cfg.nx, ny = h->cfg.ny;
+  double* S1 = h->d_stage;
+  double* S2 = h->d_stage + h->state_elems;
+  double* tp = t_dev ? t_dev : h->d_t;
+  const int rows = (in_host || out_host) ? band_rows(h) : ny;
+  const int nb = (ny + rows - 1) / rows;
+  auto r0_of = [&](int b) { return b * rows; };
+  auto r1_of = [&](int b) { return b * rows + rows < ny ? b * rows + rows : ny; };
+  cudaError_t e = cudaSuccess;
+  // ---- stage 1: bands in, wave-speed maxima, face fluxes
+  fill_faces_args(h, U, nullptr);
+  if (in_host) {
+    e = cudaEventRecord(h->band_in[8], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->band_in[8], 0);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+      e = copy_rows(h, U, in_host, r0_of(b), r1_of(b), cudaMemcpyHostToDevice, h->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(h->band_in[b], h->copy_stream);
+    }
+    // the face fluxes of band b read the rows of bands b - 1 .. b + 1
+    // (periodic wrap included), so they follow band b + 1's arrival; bands
+    // nb - 1 and 0 go last
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+      e = cudaStreamWaitEvent(s, h->band_in[b], 0);
+      if (e == cudaSuccess)
+        e = launch_cfl_mixed(ndim, U, nx, ny, h->cfg.gamma, h->d_smax, h->d_status, s, r0_of(b), r1_of(b), b == 0);
+      if (e == cudaSuccess && b >= 2) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(b - 1), r1_of(b - 1));
+    }
+    if (e == cudaSuccess && nb >= 2) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(nb - 1), r1_of(nb - 1));
+    if (e == cudaSuccess) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(0), r1_of(0));
+  } else {
+    e = launch_cfl_mixed(ndim, U, nx, ny, h->cfg.gamma, h->d_smax, h->d_status, s, 0, ny, true);
+    if (e == cudaSuccess) e = launch_faces_mixed(ndim, h->faces_args, s, 0, ny);
+  }
+  if (e == cudaSuccess) e = launch_dt(h->d_smax, ndim, h->cfg.dx, h->cfg.dy, cfl, t_end, tp, h->d_dt, dt_dev, s);
+  if (e == cudaSuccess) e = launch_diff_mixed(ndim, diff_args(h, U, U, S1, 1, tp, 0, ny), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step: first stage");
+  // ---- stage 2
+  rc = mixed_rhs(h, S1, U, S2, 2, nullptr, tp, s);
+  if (rc != NENO6_OK) return rc;
+  // ---- stage 3
+  if (!out_host) return mixed_rhs(h, S2, U, U, 3, nullptr, tp, s);
+  fill_faces_args(h, S2, nullptr);
+  e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(0), r1_of(0));
+  for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+    if (b + 1 < nb) {
+      e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(b + 1), r1_of(b + 1));
+      if (e != cudaSuccess) break;
+    }
+    e = launch_diff_mixed(ndim, diff_args(h, S2, U, U, 3, b == 0 ? tp : nullptr, r0_of(b), r1_of(b)), s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->band_done[b], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->band_done[b], 0);
+    if (e == cudaSuccess) e = copy_rows(h, out_host, U, r0_of(b), r1_of(b), cudaMemcpyDeviceToHost, h->copy_stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->band_done[8], h->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->band_done[8], 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_host: last stage in bands");
   return NENO6_OK;
 }
 
@@ -474,6 +606,11 @@ int neno6_destroy(neno6_handle* h) {
   cudaFree(h->d_vjp_contrib);
   cudaFree(h->d_params32);
   cudaFree(h->d_bwd_scratch);
+  for (cudaEvent_t ev : h->band_in)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : h->band_done)
+    if (ev) cudaEventDestroy(ev);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return NENO6_OK;
 }
@@ -522,33 +659,13 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
   if (!aligned(U, 16)) return fail(h, NENO6_ERR_ALIGN, "step: U must be 16-byte aligned");
   if (!(cfl > 0.0) || !(t_end >= 0.0)) return fail(h, NENO6_ERR_ARG, "step: need cfl > 0, t_end >= 0");
   cudaStream_t s = (cudaStream_t)stream;
-  if (!h->d_stage) {
-    cudaError_t e = cudaMalloc(&h->d_stage, 2 * h->state_elems * sizeof(double));
-    if (e != cudaSuccess) {
-      h->d_stage = nullptr;
-      return cuda_fail(h, e, "step: stage buffers");
-    }
-  }
+  int rc = ensure_stage(h);
+  if (rc != NENO6_OK) return rc;
+  if (h->cfg.precision != NENO6_FP64) return mixed_step(h, U, cfl, t_end, t_dev, dt_dev, nullptr, nullptr, s);
   double* S1 = h->d_stage;
   double* S2 = h->d_stage + h->state_elems;
-  cudaError_t e = h->cfg.precision == NENO6_FP64
-                      ? launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
-                                          h->d_status, s)
-                      : launch_cfl_mixed(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax,
-                                         h->d_status, s);
+  cudaError_t e = launch_cfl_reduce(h->cfg.ndim, U, h->cfg.nx, h->cfg.ny, h->cfg.gamma, h->d_smax, h->d_status, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step: cfl reduction");
-  if (h->cfg.precision != NENO6_FP64) {
-    double* tp = t_dev ? t_dev : h->d_t;
-    e = launch_dt(h->d_smax, h->cfg.ndim, h->cfg.dx, h->cfg.dy, cfl, t_end, tp, h->d_dt, dt_dev, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "step: dt");
-    const double* in[3] = {U, S1, S2};
-    double* outp[3] = {S1, S2, U};
-    for (int st = 1; st <= 3; ++st) {
-      int rc = mixed_rhs(h, in[st - 1], U, outp[st - 1], st, nullptr, tp, s);
-      if (rc != NENO6_OK) return rc;
-    }
-    return NENO6_OK;
-  }
   RhsParamsF64& p = h->rhs_params;
   fill_rhs_args(h, p.a);
   p.a.smax = h->d_smax;
@@ -589,15 +706,22 @@ int neno6_step_host(neno6_handle* h, const double* U_in, double* U_out, double c
     }
   }
   double* t_dev = t_io ? h->d_host_state + h->state_elems : nullptr;
-  e = cudaMemcpyAsync(h->d_host_state, U_in, bytes, cudaMemcpyHostToDevice, s);
+  // the mixed path copies the state in and out in row bands, overlapped with
+  // its first and last stages
+  const bool banded = h->cfg.precision != NENO6_FP64;
+  if (!banded) e = cudaMemcpyAsync(h->d_host_state, U_in, bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && t_io) e = cudaMemcpyAsync(t_dev, t_io, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_host: copy in");
-  const int rc = neno6_step(h, h->d_host_state, cfl, t_end, t_dev, nullptr, stream);
+  int rc = banded ? ensure_stage(h) : NENO6_OK;
+  if (rc == NENO6_OK)
+    rc = banded ? mixed_step(h, h->d_host_state, cfl, t_end, t_dev, nullptr, U_in, U_out, s)
+                : neno6_step(h, h->d_host_state, cfl, t_end, t_dev, nullptr, stream);
   if (rc != NENO6_OK) {
     cudaStreamSynchronize(s);  // the copy in reads U_in: finish it before returning
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     return rc;
   }
-  e = cudaMemcpyAsync(U_out, h->d_host_state, bytes, cudaMemcpyDeviceToHost, s);
+  if (!banded) e = cudaMemcpyAsync(U_out, h->d_host_state, bytes, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && t_io) e = cudaMemcpyAsync(t_io, t_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_host: copy out");
   e = cudaStreamSynchronize(s);

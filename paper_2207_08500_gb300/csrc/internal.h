@@ -149,8 +149,9 @@ struct FacesMixedArgs {
   double gamma, gm1;
   float cand[4][4];
   float wtab[16][4];
-  // filled by the launcher
-  long long nblk_x, nblk_y;
+  // filled by the launcher: the launched x blocks are blk_x0 .. blk_x0 +
+  // nblk_x - 1, then the y blocks blk_y0 .. blk_y0 + nblk_y - 1
+  long long blk_x0, nblk_x, blk_y0, nblk_y;
   int bxf, byc;
 };
 
@@ -161,16 +162,22 @@ struct DiffArgs {
   const double* U0;  // step start
   double* out;
   const double* dt_dev;
-  double* t_dev;
+  double* t_dev;     // stage 3 advances *t_dev by dt (when not null)
   int nx, ny, stage;
   int bcx, bcy;
+  int j0, j1;        // rows j0 .. j1 - 1
   double inv_dx, inv_dy, third, two_thirds;
 };
 
-cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s);
+// Face fluxes of the x faces of rows row0 .. row1 - 1 and of the y faces
+// row0 .. row1 - 1 (.. ny when row1 == ny); row0 and row1 multiples of 16
+// or row1 == ny.
+cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s, int row0, int row1);
 cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s);
+// Wave-speed maxima of the cells of rows row0 .. row1 - 1 folded into smax
+// (zeroed first when zero is set).
 cudaError_t launch_cfl_mixed(int ndim, const double* U, int nx, int ny, double gamma, unsigned long long* smax,
-                             int* status, cudaStream_t s);
+                             int* status, cudaStream_t s, int row0, int row1, bool zero);
 cudaError_t launch_dt(const unsigned long long* smax, int ndim, double dx, double dy, double cfl, double t_end,
                       const double* t_dev, double* dt_dev, double* dt_user, cudaStream_t s);
 

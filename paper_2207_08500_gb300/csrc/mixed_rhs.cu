@@ -209,8 +209,9 @@ __device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* w
   }
 }
 
-// Geometry of block `blk`: the x blocks come first (kLines rows x kLineFaces
-// faces), then the y blocks (kLines columns x kLineFaces faces).
+// Geometry of launched block `blk`: the x blocks come first (kLines rows x
+// kLineFaces faces), then the y blocks (kLines columns x kLineFaces faces),
+// each range starting at its launch offset.
 struct BlockGeom {
   int dir;      // 0: x faces, 1: y faces
   int row, f0;  // x block: first row, first face of each line
@@ -219,10 +220,11 @@ struct BlockGeom {
 __device__ __forceinline__ BlockGeom block_geom(long long blk, const FacesMixedArgs& a) {
   BlockGeom b{0, 0, 0, 0, 0};
   if (blk < a.nblk_x) {
+    blk += a.blk_x0;
     b.row = (int)(blk / a.bxf) * kLines;
     b.f0 = (int)(blk % a.bxf) * kLineFaces;
   } else {
-    const long long q = blk - a.nblk_x;
+    const long long q = blk - a.nblk_x + a.blk_y0;
     b.dir = 1;
     b.i0 = (int)(q % a.byc) * kLines;
     b.g0 = (int)(q / a.byc) * kLineFaces;
@@ -607,22 +609,22 @@ __global__ void __launch_bounds__(kMlpThreads, 8) faces_mixed_kernel(const __gri
   if (t < 32) tmem_dealloc(*tmem_slot, 64);
 }
 
-// Conservative difference (FP64) and optional SSP-RK3 stage update: thread
-// per cell, a 2D grid of rows (blockIdx.y, grid-stride beyond 65535 rows) by
-// runs of 256 cells.  The difference of each direction is one DADD and the
+// Conservative difference (FP64) and optional SSP-RK3 stage update of the
+// rows j0 .. j1 - 1: thread per cell, a 2D grid of rows (blockIdx.y,
+// grid-stride beyond 65535 rows) by runs of 256 cells.  The difference of each direction is one DADD and the
 // two directions combine in one DMUL + DFMA: 4 FP64 operations per field.
 template <int NDIM>
 __global__ void __launch_bounds__(256) diff_mixed_kernel(DiffArgs a) {
   constexpr int NV = NDIM == 2 ? 4 : 3;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double dt = a.stage ? *a.dt_dev : 0.0;
-  if (a.stage == 3 && i == 0 && blockIdx.y == 0) *a.t_dev = *a.t_dev + dt;
+  if (a.stage == 3 && a.t_dev && i == 0 && blockIdx.y == 0) *a.t_dev = *a.t_dev + dt;
   if (i >= a.nx) return;
   const size_t plane = (size_t)a.nx * a.ny;
   // with periodic boundaries faces 0 and nx (ny) are one physical face: both
   // neighbours use face 0's value, so the difference telescopes exactly
   const int ir = (i + 1 == a.nx && a.bcx == 0) ? 0 : i + 1;
-  for (int j = blockIdx.y; j < a.ny; j += gridDim.y) {
+  for (int j = a.j0 + (int)blockIdx.y; j < a.j1; j += gridDim.y) {
     const int jr = (j + 1 == a.ny && a.bcy == 0) ? 0 : j + 1;
     const size_t cell = (size_t)j * a.nx + i;
 #pragma unroll
@@ -654,13 +656,14 @@ __global__ void __launch_bounds__(256) diff_mixed_kernel(DiffArgs a) {
 // path's (non-negative values order like their patterns).
 template <int NDIM>
 __global__ void __launch_bounds__(256) cfl_mixed_kernel(const double* __restrict__ U, int nx, int ny,
-                                                        double gamma, unsigned long long* smax, int* status) {
+                                                        size_t k0, size_t k1, double gamma,
+                                                        unsigned long long* smax, int* status) {
   const size_t plane = (size_t)nx * ny;
   const double gm1 = gamma - 1.0;
   const float gamma_f = (float)gamma;
   float mx = 0.0f, my = 0.0f;
   bool bad = false;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
+  for (size_t k = k0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < k1;
        k += (size_t)gridDim.x * blockDim.x) {
     const double rho = U[k];
     const double m = U[plane + k];
@@ -713,14 +716,23 @@ void build_guard_image(const NetF64& net, float* g) {
   }
 }
 
-cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
+cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s, int row0, int row1) {
   // x blocks: nx + 1 faces per row in runs of kLineFaces, rows in groups of
   // kLines; y blocks: columns in groups of kLines, ny + 1 faces per column
+  // in runs of kLineFaces.  Rows row0 .. row1 - 1: their row groups, and the
+  // runs of y faces from row0 up to row1 (the last run when row1 == ny).
   a.bxf = (a.nx + 1 + kLineFaces - 1) / kLineFaces;
-  a.nblk_x = (long long)a.bxf * ((a.ny + kLines - 1) / kLines);
   a.byc = (a.nx + kLines - 1) / kLines;
-  a.nblk_y = ndim == 2 ? (long long)a.byc * ((a.ny + 1 + kLineFaces - 1) / kLineFaces) : 0;
+  const int rg0 = row0 / kLines;
+  const int rg1 = row1 == a.ny ? (a.ny + kLines - 1) / kLines : row1 / kLines;
+  const int fr0 = row0 / kLineFaces;
+  const int fr1 = row1 == a.ny ? (a.ny + 1 + kLineFaces - 1) / kLineFaces : row1 / kLineFaces;
+  a.blk_x0 = (long long)a.bxf * rg0;
+  a.nblk_x = (long long)a.bxf * (rg1 - rg0);
+  a.blk_y0 = (long long)a.byc * fr0;
+  a.nblk_y = ndim == 2 ? (long long)a.byc * (fr1 - fr0) : 0;
   const long long nblk = a.nblk_x + a.nblk_y;
+  if (nblk <= 0) return cudaSuccess;
   // persistent grid: eight resident CTAs per SM (registers, shared memory,
   // 64 TMEM columns each)
   const int blocks = (int)(nblk < 152 * 8 ? nblk : 152 * 8);
@@ -733,21 +745,26 @@ cudaError_t launch_faces_mixed(int ndim, FacesMixedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_diff_mixed(int ndim, const DiffArgs& a, cudaStream_t s) {
-  const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535));
+  const int rows = a.j1 - a.j0;
+  if (rows <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
   if (ndim == 2) diff_mixed_kernel<2><<<grid, 256, 0, s>>>(a);
   else diff_mixed_kernel<1><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cfl_mixed(int ndim, const double* U, int nx, int ny, double gamma, unsigned long long* smax,
-                             int* status, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  const size_t cells = (size_t)nx * ny;
-  unsigned blocks = (unsigned)((cells + 255) / 256);
+                             int* status, cudaStream_t s, int row0, int row1, bool zero) {
+  if (zero) {
+    cudaError_t e = cudaMemsetAsync(smax, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+  }
+  const size_t k0 = (size_t)row0 * nx, k1 = (size_t)row1 * nx;
+  if (k1 <= k0) return cudaSuccess;
+  unsigned blocks = (unsigned)((k1 - k0 + 255) / 256);
   if (blocks > 152u * 8u) blocks = 152u * 8u;
-  if (ndim == 2) cfl_mixed_kernel<2><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
-  else cfl_mixed_kernel<1><<<blocks, 256, 0, s>>>(U, nx, ny, gamma, smax, status);
+  if (ndim == 2) cfl_mixed_kernel<2><<<blocks, 256, 0, s>>>(U, nx, ny, k0, k1, gamma, smax, status);
+  else cfl_mixed_kernel<1><<<blocks, 256, 0, s>>>(U, nx, ny, k0, k1, gamma, smax, status);
   return cudaGetLastError();
 }
 

@@ -108,3 +108,25 @@ def test_mixed_step_close_to_fp64(lib, wpath):
     print("state rel L1 after 3 steps: %.3e" % err)
     assert err < 1e-6
     assert abs(ta.item() - tb.item()) <= 1e-6 * ta.item()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("nx,ny,bc", [(200, 136, ("periodic", "periodic")),
+                                      (67, 33, ("transmissive", "transmissive"))])
+def test_mixed_rhs_trained_network_bounds(lib, prec, nx, ny, bc):
+    """The trained classifier (default weights, default guard bands) at the
+    parity sizes, held to the mixed-precision targets: decision flip rate at
+    most 1e-5 and dU/dt within 1e-6 relative L1 of the FP64 path (the
+    random network above is dense in near-zero logits and pins little)."""
+    g64 = lib.Neno6(precision="fp64", ndim=2, nx=nx, ny=ny, bc=bc)
+    gmx = lib.Neno6(precision=prec, ndim=2, nx=nx, ny=ny, bc=bc)
+    Ud = torch.from_numpy(synth.quadrants_2d(nx, ny, seed=5)).cuda()
+    d64, m64 = g64.rhs(Ud, want_mask=True)
+    dmx, mmx = gmx.rhs(Ud, want_mask=True)
+    m64, mmx = m64.cpu().numpy(), mmx.cpu().numpy()
+    flips = np.unpackbits(m64 ^ mmx).sum() / (8.0 * m64.size)
+    err = rel_l1(dmx.cpu().numpy(), d64.cpu().numpy())
+    print("trained %s %dx%d: flip rate %.3e, rel L1 %.3e" % (prec, nx, ny, flips, err))
+    assert flips <= 1e-5
+    assert err <= 1e-6
+    assert gmx.status() == 0
