@@ -687,6 +687,46 @@ def run_rhs_only(args):
                       "launches": args.warmup + args.steps, "status": g.status()}))
 
 
+def run_mlp_bwd_only(args):
+    """`--mlp-bwd-only`: warm-up + `--steps` classifier gradients (Eq.
+    (Crossentropy)) on 2^20 synthetic stencils with a mixed-precision handle
+    (the tensor-core kernel; `--precision fp64` gives the FP32 CUDA-core
+    kernel), a case for profilers; prints one line, no timing."""
+    import torch
+    import paper_2207_08500_gb300 as neno6
+    import synth
+    n = 1 << 20
+    g = neno6.Neno6(ndim=1, nx=8, precision=args.precision, weights=args.weights)
+    X = torch.from_numpy(synth.mlp_stencils(n)).cuda()
+    y = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    y[n // 2:] = 0b1011
+    for _ in range(args.warmup + args.steps):
+        g.mlp_bwd(X, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"mlp_bwd_only": True, "n": n, "precision": args.precision,
+                      "launches": args.warmup + args.steps, "status": g.status()}))
+
+
+def run_mlp_train_only(args):
+    """`--mlp-train-only`: warm-up + `--steps` calls of the training loop
+    (Sec. 3.3, Table 2: Adam, batch 175) over 100 batches of Table 9 samples
+    generated on the GPU, a case for profilers; prints one line, no timing."""
+    import torch
+    import paper_2207_08500_gb300 as neno6
+    g = neno6.Neno6(ndim=1, nx=8, weights=args.weights)
+    n = 175 * 100
+    u = torch.from_numpy(np.random.default_rng(17).random((n, neno6.DATAGEN_DRAWS))).cuda()
+    X, y, _ = g.datagen(u)
+    perm = torch.randperm(n, generator=torch.Generator().manual_seed(15)).to("cuda", torch.int32)
+    params = torch.from_numpy(he_init_params(seed=16)).cuda()
+    m, v = torch.zeros_like(params), torch.zeros_like(params)
+    for k in range(args.warmup + args.steps):
+        g.mlp_train(X, y, perm, params, m, v, 100 * k, 1e-4)
+    torch.cuda.synchronize()
+    print(json.dumps({"mlp_train_only": True, "samples": n, "batch": 175,
+                      "launches": args.warmup + args.steps, "status": g.status()}))
+
+
 def run_classify_only(args):
     """`--classify-only`: warm-up + `--steps` neno6_classify calls on `--n`
     sine / step stencils with the paper's network, then the same with the
@@ -788,6 +828,8 @@ def main():
     ap.add_argument("--rhs-only", action="store_true")
     ap.add_argument("--vjp-only", action="store_true")
     ap.add_argument("--classify-only", action="store_true")
+    ap.add_argument("--mlp-bwd-only", action="store_true")
+    ap.add_argument("--mlp-train-only", action="store_true")
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--ref-crop", type=int, default=192)
     ap.add_argument("--cpu-sizes", default="256,1024,2048")
@@ -795,6 +837,12 @@ def main():
     args = ap.parse_args()
     if args.workload == "oblique" and args.impl == "ours":
         print(json.dumps(run_oblique(args)))
+        return
+    if args.mlp_bwd_only:
+        run_mlp_bwd_only(args)
+        return
+    if args.mlp_train_only:
+        run_mlp_train_only(args)
         return
     if args.classify_only:
         args.n = args.n or (1 << 20)
