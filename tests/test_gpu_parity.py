@@ -1,9 +1,9 @@
 """Parity of the CUDA FP64 path with the FP64 oracle, through the C ABI.
 
 The FP64 path evaluates every quantity in the same order as the oracle, so
-the expectation is bit-exact classifier masks (the spec requirement)
-and bit-exact states; the state tolerance written in the tests is the
-north-star's relative L1 <= 1e-12, with the exact-match count asserted
+the expectation is bit-exact classifier masks (required of the FP64 form)
+and bit-exact states; the state tolerance written in the tests is the FP64
+form's relative L1 <= 1e-12, with the exact-match count asserted
 separately.
 """
 import numpy as np

@@ -2,7 +2,7 @@
 the FP64 right-hand side against the FP64 oracle, through the C ABI: the
 selection runs on the split characteristic fluxes in place of the
 classifier, in the same canonical arithmetic order on both sides, so masks,
-dU/dt and states are compared bit for bit (the spec FP64 tolerance,
+dU/dt and states are compared bit for bit (the FP64 form's tolerance,
 relative L1 <= 1e-12, is asserted as well)."""
 import numpy as np
 import pytest

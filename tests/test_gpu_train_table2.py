@@ -1,5 +1,5 @@
-"""Algorithm 1 and the Table 2 training recipe run entirely on the GPU, judged
-by the FP64 oracle classifier on held-out data.
+"""Algorithm 1 and the Table 2 training recipe run entirely on the GPU,
+evaluated by the FP64 oracle classifier on held-out data.
 
 709 000 samples of Table 9 are generated on the device (neno6_datagen) from
 seeded uniform draws; the first 70 % train the 6-64-32-16-8-4 network with

@@ -367,7 +367,7 @@ def test_first_order_roe_llf_closed_form(oracle_mod):
 def test_euler_order_of_accuracy(oracle_mod, kind, order):
     """All stencils smooth on a smooth periodic density wave (u, p uniform):
     the Euler RHS converges at fourth order with the paper's d, at sixth order
-    with the sixth-order d (spec check of the linear background scheme)."""
+    with the sixth-order d (the check of the linear background scheme)."""
     errs = []
     for N in (16, 32, 64):
         x = (np.arange(N) + 0.5) / N
