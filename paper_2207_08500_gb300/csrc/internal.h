@@ -72,16 +72,22 @@ struct ClassifyParamsF64 {
 
 // Tensor-core image of the classifier (mixed precision): layers 1-4 as 16-bit
 // B operands W_l[out][in] in the K-major canonical layout (K of layer 1
-// padded 6 -> 16, N of layer 4 padded 8 -> 16 with zero rows).  The biases of
-// layers 1 and 2 ride on the tensor cores: the layer-1 input row carries 1 in
-// columns kOnesCol..kOnesCol+2, B1 holds b1 split into three 16-bit terms
-// (hi + mid + lo, ~24 significant bits) in those columns, and a fifth K-step
-// of layer 2 multiplies the same input tile by the 32 x 16 tile B2b that
-// holds b2's three terms in those columns (zero elsewhere).  Then the FP32
+// padded to 16, N of layer 4 padded 8 -> 16 with zero rows).  Layer 1's
+// weights are split into two 16-bit terms, W1 = hi + lo (columns 0-5 hold hi,
+// 6-11 lo), and the layer-1 input row carries the six stencil values in
+// columns 0-5 and again in 6-11: the layer-1 products then see W1 to ~16
+// (bf16) or ~22 (fp16) significant bits.  On smooth stencils the first layer's
+// weights nearly cancel against the stencil's mean, and a single 16-bit
+// rounding of W1 leaves a residue of the mean larger than the stencil's own
+// variation.  The biases of layers 1 and 2 ride on the tensor cores: the
+// input row carries 1 in columns kOnesCol..kOnesCol+2, B1 holds b1 split into
+// three 16-bit terms (hi + mid + lo, ~24 significant bits) in those columns,
+// and a fifth K-step of layer 2 multiplies the same input tile by the 32 x 16
+// tile B2b that holds b2's three terms in those columns (zero elsewhere).  Then the FP32
 // biases of layers 3-5 (b3 at 0, b4 at 16, b5 at 24) and the FP32 weights of
 // layer 5, stored transposed (W5^T[8][4]) for packed two-output FMAs on the
 // CUDA cores.
-constexpr int kOnesCol = 6;
+constexpr int kOnesCol = 12;
 constexpr int kNetImageB1 = 0;                           // 64 x 16
 constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;   // 32 x 64
 constexpr int kNetImageB2b = kNetImageB2 + 32 * 64 * 2;  // 32 x 16

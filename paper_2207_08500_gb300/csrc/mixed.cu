@@ -157,6 +157,13 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
       b -= from_16_bits(h, bf16);
     }
   };
+  // layer-1 weight w of output n, input i: hi in column i, lo = the 16-bit
+  // rounding of w - hi in column 6 + i
+  auto put_w1 = [&](int off, int n, int i, double w) {
+    const uint16_t h = bits(w);
+    put_bits(off, 16, n, i, h);
+    put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
+  };
   const int widths[6] = {6, 64, 32, 16, 8, 4};
   const int boff[4] = {kNetImageB1, kNetImageB2, kNetImageB3, kNetImageB4};
   const int Kpad[4] = {16, 64, 32, 16};
@@ -168,7 +175,8 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
     for (int o = 0; o < nout; ++o)
       for (int i = 0; i < nin; ++i) {
         const double w = net.p[p + (size_t)o * nin + i];
-        if (l < 4) put_bits(boff[l], Kpad[l], o, i, bits(w));
+        if (l == 0) put_w1(boff[0], o, i, w);
+        else if (l < 4) put_bits(boff[l], Kpad[l], o, i, bits(w));
         else w5t[i * 4 + o] = (float)w;
       }
     p += (size_t)nout * nin;
@@ -214,6 +222,11 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
       b -= from_16_bits(h, bf16);
     }
   };
+  auto put_w1 = [&](int off, int n, int i, double w) {  // hi in column i, lo in 6 + i
+    const uint16_t h = bits(w);
+    put_bits(off, 16, n, i, h);
+    put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
+  };
   const int boff[3] = {kNarrowB1, kNarrowB2, kNarrowB3};
   const int Kpad[3] = {16, 32, 32};
   float* b3 = reinterpret_cast<float*>(img + kNarrowBias3);
@@ -224,7 +237,8 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
     for (int o = 0; o < nout; ++o)
       for (int i = 0; i < nin; ++i) {
         const double w = net.p[p + (size_t)o * nin + i];
-        if (l < 3) put_bits(boff[l], Kpad[l], o, i, bits(w));
+        if (l == 0) put_w1(boff[0], o, i, w);
+        else if (l < 3) put_bits(boff[l], Kpad[l], o, i, bits(w));
         else w4t[i * 4 + o] = (float)w;
       }
     p += (size_t)nout * nin;
