@@ -17,9 +17,9 @@ For each weights file the script reports
 The 16-bit evaluation follows the arithmetic of the library's tensor-core
 classifier: the normalised input (Eq. for X, FP32, divided by max(|x|, 1)) and
 every weight of a tensor-core layer are rounded to 16 bits (round to nearest
-even), except that the first layer's weights are carried as two 16-bit terms
-(hi, then the rounding of what hi leaves), products are summed in FP32 and the
-bias is added in FP32; a hidden
+even), except that in bf16 the first layer's weights are carried as two
+16-bit terms (hi, then the rounding of what hi leaves), products are summed in
+FP32 and the bias is added in FP32; a hidden
 activation is ReLU'd and rounded to 16 bits when the next layer is also a
 tensor-core layer.  Every layer but the last runs on the tensor cores; the
 last layer (8 -> 4, or 32 -> 4) takes the FP32 activation and FP32 weights on
@@ -98,7 +98,7 @@ def forward16(net, X, prec):
         if li + 1 < L:
             W32 = W.astype(np.float32)
             Wr = rnd(W32)
-            if li == 0 and prec is not None:
+            if li == 0 and prec == "bf16":
                 Wr = Wr + rnd(W32 - Wr)  # hi + lo: exact in FP32
             z = a @ Wr.T + b32
             h = np.maximum(z, np.float32(0.0))

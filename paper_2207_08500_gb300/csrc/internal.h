@@ -72,14 +72,16 @@ struct ClassifyParamsF64 {
 
 // Tensor-core image of the classifier (mixed precision): layers 1-4 as 16-bit
 // B operands W_l[out][in] in the K-major canonical layout (K of layer 1
-// padded to 16, N of layer 4 padded 8 -> 16 with zero rows).  Layer 1's
-// weights are split into two 16-bit terms, W1 = hi + lo (columns 0-5 hold hi,
-// 6-11 lo), and the layer-1 input row carries the six stencil values in
-// columns 0-5 and again in 6-11: the layer-1 products then see W1 to ~16
-// (bf16) or ~22 (fp16) significant bits.  On smooth stencils the first layer's
-// weights nearly cancel against the stencil's mean, and a single 16-bit
+// padded to 16, N of layer 4 padded 8 -> 16 with zero rows).  In the bf16
+// image layer 1's weights are split into two 16-bit terms, W1 = hi + lo
+// (columns 0-5 hold hi, 6-11 lo), and the layer-1 input row carries the six
+// stencil values in columns 0-5 and again in 6-11: the layer-1 products then
+// see W1 to ~16 significant bits.  On smooth stencils the first layer's
+// weights nearly cancel against the stencil's mean, and a single bf16
 // rounding of W1 leaves a residue of the mean larger than the stencil's own
-// variation.  The biases of layers 1 and 2 ride on the tensor cores: the
+// variation.  The fp16 image keeps the single rounding (lo columns zero):
+// at 11 bits the residue stays below the variation.  The biases of layers 1
+// and 2 ride on the tensor cores: the
 // input row carries 1 in columns kOnesCol..kOnesCol+2, B1 holds b1 split into
 // three 16-bit terms (hi + mid + lo, ~24 significant bits) in those columns,
 // and a fifth K-step of layer 2 multiplies the same input tile by the 32 x 16

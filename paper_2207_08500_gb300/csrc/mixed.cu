@@ -158,11 +158,12 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
     }
   };
   // layer-1 weight w of output n, input i: hi in column i, lo = the 16-bit
-  // rounding of w - hi in column 6 + i
+  // rounding of w - hi in column 6 + i (bf16; fp16 keeps the single
+  // rounding, lo = 0)
   auto put_w1 = [&](int off, int n, int i, double w) {
     const uint16_t h = bits(w);
     put_bits(off, 16, n, i, h);
-    put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
+    if (bf16) put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
   };
   const int widths[6] = {6, 64, 32, 16, 8, 4};
   const int boff[4] = {kNetImageB1, kNetImageB2, kNetImageB3, kNetImageB4};
@@ -222,10 +223,10 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
       b -= from_16_bits(h, bf16);
     }
   };
-  auto put_w1 = [&](int off, int n, int i, double w) {  // hi in column i, lo in 6 + i
+  auto put_w1 = [&](int off, int n, int i, double w) {  // hi in column i, lo in 6 + i (bf16)
     const uint16_t h = bits(w);
     put_bits(off, 16, n, i, h);
-    put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
+    if (bf16) put_bits(off, 16, n, 6 + i, bits(w - from_16_bits(h, bf16)));
   };
   const int boff[3] = {kNarrowB1, kNarrowB2, kNarrowB3};
   const int Kpad[3] = {16, 32, 32};

@@ -39,15 +39,15 @@ def round16(a, kind):
 
 
 def emulate(net, X, kind):
-    """Layers 1-4 with 16-bit inputs and weights (tensor cores; layer 1's
-    weights as two 16-bit terms, hi and the rounding of what hi leaves),
+    """Layers 1-4 with 16-bit inputs and weights (tensor cores; in bf16 layer
+    1's weights as two 16-bit terms, hi and the rounding of what hi leaves),
     layer 5 in FP32 (CUDA cores), biases at (at least) FP32 precision."""
     x = np.asarray(X, dtype=np.float32)
     m = np.maximum(1.0, np.abs(x).max(axis=1)).astype(np.float32)
     h = round16(x / m[:, None], kind)
     L = len(net.layers)
     for l, (W, b) in enumerate(net.layers):
-        if l == 0:
+        if l == 0 and kind == "bf16":
             W32 = np.asarray(W, dtype=np.float32)
             hi = round16(W32, kind)
             Wr = (hi + round16(W32 - hi, kind)).astype(np.float64)
