@@ -519,10 +519,10 @@ PRECISION_NOTE = {
 # ncu capture of the current kernels at the grid named (dram__bytes_read.sum
 # + dram__bytes_write.sum, a single-pass capture); other grids: None
 TRAFFIC = {True: (2048, 141937152 + 94543104),
-           False: (4096, 1199868672 + 1050030336 + 1074064128 + 507846144)}
+           False: (4096, 1212746496 + 1051745536 + 1074054656 + 507911424)}
 TRAFFIC_NOTE = {True: "rhs_fp64_kernel at 2048^2, one launch: 141.9 MB read + 94.5 MB written",
-                False: "one RHS at 4096^2: faces_mixed_kernel 1199.9 MB read + 1050.0 MB written, "
-                       "diff_mixed_kernel 1074.1 MB read + 507.8 MB written"}
+                False: "one RHS at 4096^2: faces_mixed_kernel 1212.7 MB read + 1051.7 MB written, "
+                       "diff_mixed_kernel 1074.1 MB read + 507.9 MB written"}
 
 
 def traffic_bytes(prec, n):

@@ -79,17 +79,18 @@ struct ClassifyParamsF64 {
 // see W1 to ~16 significant bits.  On smooth stencils the first layer's
 // weights nearly cancel against the stencil's mean, and a single bf16
 // rounding of W1 leaves a residue of the mean larger than the stencil's own
-// variation.  The fp16 image keeps the single rounding (lo columns zero):
-// at 11 bits the residue stays below the variation.  The biases of layers 1
-// and 2 ride on the tensor cores: the
-// input row carries 1 in columns kOnesCol..kOnesCol+2, B1 holds b1 split into
+// variation.  The fp16 image keeps the single rounding and the plain row
+// (stencil values in columns 0-5 only): at 11 bits the residue stays below
+// the variation.  The biases of layers 1 and 2 ride on the tensor cores: the
+// input row carries 1 in columns ones_col .. ones_col + 2 (6-8 in fp16, 12-14
+// in bf16), B1 holds b1 split into
 // three 16-bit terms (hi + mid + lo, ~24 significant bits) in those columns,
 // and a fifth K-step of layer 2 multiplies the same input tile by the 32 x 16
 // tile B2b that holds b2's three terms in those columns (zero elsewhere).  Then the FP32
 // biases of layers 3-5 (b3 at 0, b4 at 16, b5 at 24) and the FP32 weights of
 // layer 5, stored transposed (W5^T[8][4]) for packed two-output FMAs on the
 // CUDA cores.
-constexpr int kOnesCol = 12;
+__host__ __device__ constexpr int ones_col(bool bf16) { return bf16 ? 12 : 6; }
 constexpr int kNetImageB1 = 0;                           // 64 x 16
 constexpr int kNetImageB2 = kNetImageB1 + 64 * 16 * 2;   // 32 x 64
 constexpr int kNetImageB2b = kNetImageB2 + 32 * 64 * 2;  // 32 x 16

@@ -13,7 +13,7 @@
 // (bounded), loads its row of the FP32 accumulator from TMEM, applies ReLU,
 // rounds to bf16/fp16 (one packed cvt per pair) and stores it as its row of
 // the next layer's input.  The biases of layers 1 and 2 are accumulated by
-// the tensor cores (constant-one input columns, see kOnesCol); the biases of
+// the tensor cores (constant-one input columns, see ones_col); the biases of
 // layers 3-4 are added in FP32 in the epilogues, and layer 5 (8 -> 4) runs
 // in FP32 on the CUDA cores.  64 TMEM columns per CTA.
 #include <cuda_bf16.h>
@@ -153,7 +153,7 @@ void build_net_image(const NetF64& net, bool bf16, uint8_t* img) {
   auto put_bias = [&](int off, int K, int n, double b) {
     for (int q = 0; q < 3; ++q) {
       const uint16_t h = bits(b);
-      put_bits(off, K, n, kOnesCol + q, h);
+      put_bits(off, K, n, ones_col(bf16) + q, h);
       b -= from_16_bits(h, bf16);
     }
   };
@@ -219,7 +219,7 @@ void build_net_image_narrow(const NetF64& net, bool bf16, uint8_t* img) {
   auto put_bias = [&](int off, int n, double b) {
     for (int q = 0; q < 3; ++q) {
       const uint16_t h = bits(b);
-      put_bits(off, 16, n, kOnesCol + q, h);
+      put_bits(off, 16, n, ones_col(bf16) + q, h);
       b -= from_16_bits(h, bf16);
     }
   };

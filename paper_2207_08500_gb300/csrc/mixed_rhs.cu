@@ -174,19 +174,17 @@ __device__ __forceinline__ void guard_mlp(const float* __restrict__ gw, float* w
     }
     __syncwarp();
     {
-      // four partial sums (inputs i = q mod 4): 16 weight loads in flight
-      // and FMA chains a quarter as long
-      float acc[4] = {__ldg(gw + 2496 + lane), 0.0f, 0.0f, 0.0f};
-#pragma unroll 16
-      for (int i = 0; i < 64; ++i) acc[i & 3] = fmaf(__ldg(gw + 448 + i * 32 + lane), ws[i], acc[i & 3]);
-      ws[64 + lane] = fmaxf((acc[0] + acc[1]) + (acc[2] + acc[3]), 0.0f);
+      float acc = gw[2496 + lane];
+#pragma unroll 8
+      for (int i = 0; i < 64; ++i) acc = fmaf(gw[448 + i * 32 + lane], ws[i], acc);
+      ws[64 + lane] = fmaxf(acc, 0.0f);
     }
     __syncwarp();
     if (lane < 16) {
-      float acc[4] = {__ldg(gw + 3040 + lane), 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i & 3] = fmaf(__ldg(gw + 2528 + i * 16 + lane), ws[64 + i], acc[i & 3]);
-      ws[96 + lane] = fmaxf((acc[0] + acc[1]) + (acc[2] + acc[3]), 0.0f);
+      float acc = gw[3040 + lane];
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) acc = fmaf(gw[2528 + i * 16 + lane], ws[64 + i], acc);
+      ws[96 + lane] = fmaxf(acc, 0.0f);
     }
     __syncwarp();
     if (lane < 8) {

@@ -64,15 +64,20 @@ __device__ __forceinline__ void st_row8(uint8_t* base, int row, int k0, int K, u
 }
 
 // Row `row` of the layer-1 input tile (K = 16): the six normalised stencil
-// values in columns 0-5 (against W1's hi terms) and again in 6-11 (against
-// its lo terms), then 1, 1, 1 in columns kOnesCol..kOnesCol+2 (bias terms),
-// zero.
+// values in columns 0-5 and, in bf16, again in 6-11 (against W1's hi and lo
+// terms), then 1, 1, 1 in columns ones_col(BF16) .. + 2 (bias terms), zeros.
 template <bool BF16>
 __device__ __forceinline__ void store_input_row(uint8_t* bufY, int row, const float x[6]) {
-  static_assert(kOnesCol == 12, "ones occupy columns 12-14");
   const uint32_t p01 = pack2<BF16>(x[0], x[1]), p23 = pack2<BF16>(x[2], x[3]), p45 = pack2<BF16>(x[4], x[5]);
-  st_row8(bufY, row, 0, 16, p01, p23, p45, p01);
-  st_row8(bufY, row, 8, 16, p23, p45, ones2<BF16>(), one0<BF16>());
+  if (BF16) {
+    static_assert(ones_col(true) == 12, "bf16: ones occupy columns 12-14");
+    st_row8(bufY, row, 0, 16, p01, p23, p45, p01);
+    st_row8(bufY, row, 8, 16, p23, p45, ones2<BF16>(), one0<BF16>());
+  } else {
+    static_assert(ones_col(false) == 6, "fp16: ones occupy columns 6-8");
+    st_row8(bufY, row, 0, 16, p01, p23, p45, ones2<BF16>());
+    st_row8(bufY, row, 8, 16, one0<BF16>(), 0u, 0u, 0u);
+  }
 }
 
 struct MlpCtx {
@@ -87,7 +92,7 @@ struct MlpCtx {
 
 // Issue one layer (thread 0): K/16 MMAs of K = 16 into TMEM column `col`,
 // plus, if Bb_off >= 0, a bias K-step (the layer-1 input tile in bufY, whose
-// columns kOnesCol..kOnesCol+2 hold 1, times the bias tile at Bb_off).
+// columns ones_col .. ones_col + 2 hold 1, times the bias tile at Bb_off).
 template <bool BF16>
 __device__ __forceinline__ void issue_layer(const MlpCtx& c, const uint8_t* A, int K, int B_off, int N,
                                             int col, int Bb_off = -1) {
