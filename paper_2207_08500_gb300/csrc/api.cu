@@ -431,8 +431,9 @@ cudaError_t copy_rows(const neno6_handle* h, double* dst, const double* src, int
 // With in_host / out_host (neno6_step_host), U is filled from in_host and
 // copied to out_host in row bands on the handle's copy stream, overlapped
 // with compute: the first stage's face fluxes (which do not depend on dt)
-// and the wave-speed maxima of each band start as soon as the band and its
-// neighbours have arrived, only the first stage's difference waits for dt;
+// and the wave-speed maxima of each band start as soon as the band and the
+// rows its stencils read have arrived, only the first stage's difference
+// waits for dt;
 // the last stage runs band by band (face kernel of band b + 1, then the
 // difference of band b, whose top row needs the first y faces of band b + 1),
 // each band copied out as it finishes.  The arithmetic of every face and
@@ -455,23 +456,32 @@ int mixed_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
   // ---- stage 1: bands in, wave-speed maxima, face fluxes
   fill_faces_args(h, U, nullptr);
   if (in_host) {
+    // A band's y faces read three rows of each neighbouring band, so the
+    // copies run: the last band's final kHalo rows (the periodic wrap of band
+    // 0), then each band with the first kHalo rows of the next; band b's
+    // wave-speed maxima and face fluxes start as soon as that much is in.
+    constexpr int kHalo = 16;
+    const int tail0 = nb >= 2 ? ny - kHalo : ny;
     e = cudaEventRecord(h->band_in[8], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->band_in[8], 0);
+    if (e == cudaSuccess && tail0 < ny)
+      e = copy_rows(h, U, in_host, tail0, ny, cudaMemcpyHostToDevice, h->copy_stream);
+    int copied = 0;  // rows [0, copied) are in (and [tail0, ny))
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {
-      e = copy_rows(h, U, in_host, r0_of(b), r1_of(b), cudaMemcpyHostToDevice, h->copy_stream);
+      int hi = b + 1 < nb ? r1_of(b) + kHalo : tail0;
+      if (hi > tail0) hi = tail0;
+      if (hi > copied) {
+        e = copy_rows(h, U, in_host, copied, hi, cudaMemcpyHostToDevice, h->copy_stream);
+        copied = hi;
+      }
       if (e == cudaSuccess) e = cudaEventRecord(h->band_in[b], h->copy_stream);
     }
-    // the face fluxes of band b read the rows of bands b - 1 .. b + 1
-    // (periodic wrap included), so they follow band b + 1's arrival; bands
-    // nb - 1 and 0 go last
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {
       e = cudaStreamWaitEvent(s, h->band_in[b], 0);
       if (e == cudaSuccess)
         e = launch_cfl_mixed(ndim, U, nx, ny, h->cfg.gamma, h->d_smax, h->d_status, s, r0_of(b), r1_of(b), b == 0);
-      if (e == cudaSuccess && b >= 2) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(b - 1), r1_of(b - 1));
+      if (e == cudaSuccess) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(b), r1_of(b));
     }
-    if (e == cudaSuccess && nb >= 2) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(nb - 1), r1_of(nb - 1));
-    if (e == cudaSuccess) e = launch_faces_mixed(ndim, h->faces_args, s, r0_of(0), r1_of(0));
   } else {
     e = launch_cfl_mixed(ndim, U, nx, ny, h->cfg.gamma, h->d_smax, h->d_status, s, 0, ny, true);
     if (e == cudaSuccess) e = launch_faces_mixed(ndim, h->faces_args, s, 0, ny);
