@@ -69,3 +69,15 @@ def test_step_host_clips_to_t_end(lib, wpath):
     t_dev = torch.full((1,), 0.5 * t_end, dtype=torch.float64, device="cuda")
     g.step(ref, 0.4, t_end=t_end, t=t_dev)
     assert torch.equal(out, ref.cpu())
+
+
+def test_step_host_1d_mixed(lib):
+    """1D mixed-precision handle: one band, copies in and out around it."""
+    g = lib.Neno6(ndim=1, nx=400, bc=("transmissive", "transmissive"), precision="fp16")
+    U0 = synth.riemann_1d(400, seed=3)
+    Ud = torch.from_numpy(U0.copy()).cuda()
+    t_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.step(Ud, 0.5, t=t_dev)
+    out, t = g.step_host(torch.from_numpy(U0.copy()).pin_memory(), 0.5, t=0.0)
+    assert torch.equal(out, Ud.cpu())
+    assert t == t_dev.item()
