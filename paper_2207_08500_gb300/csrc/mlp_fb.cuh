@@ -136,6 +136,130 @@ __device__ __forceinline__ void sample_fwd_bwd(const float* W, float* st, int co
   }
 }
 
+// The same forward and backward pass, the CTA's NW warps cooperating on up
+// to 32 samples (lane = sample = staged column `col`): every layer's outputs
+// are split among the warps (output o to warp o % NW), each output computed
+// exactly as above -- its bias (or 0), then an fma chain over its inputs in
+// ascending order, the inputs read back from the staged rows -- with a CTA
+// barrier between layers; warp 0 forms the outputs, the loss and dL/dz.  The
+// staged rows are therefore bit for bit those of sample_fwd_bwd, in a
+// quarter of its latency with four warps.  Every thread of the CTA must call
+// it: lanes with `active` false (no staged column) only meet the barriers,
+// active lanes past the batch pass `live` false.
+template <int PITCH, int NW, int kG = 8>
+__device__ __forceinline__ void sample_fwd_bwd_coop(const float* W, float* st, int col, int warp, bool active,
+                                                    bool live, const float (&xr)[6], unsigned lab, float inv_nS,
+                                                    double& loss) {
+  if (warp == 0 && active) {
+    float x0[6], m = 1.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      x0[j] = live ? xr[j] : 0.0f;
+      m = fmaxf(m, fabsf(x0[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) st[(kX0 + j) * PITCH + col] = x0[j] / m;
+  }
+  __syncthreads();
+  // hidden layers l = 0..3: input rows xin, output rows xout
+#pragma unroll 1
+  for (int l = 0; l < 4; ++l) {
+    const int nin = wid(l), nout = wid(l + 1);
+    const int xin = l == 0 ? kX0 : l == 1 ? kX1 : l == 2 ? kX2 : kX3;
+    const int xout = l == 0 ? kX1 : l == 1 ? kX2 : l == 2 ? kX3 : kX4;
+    const float* Wl = W + wofs(l);
+    // kG of this warp's outputs at a time (o0, o0 + NW, ...), independent
+    // chains over one pass of the inputs
+#pragma unroll 1
+    for (int o0 = warp; active && o0 < nout; o0 += NW * kG) {
+      float a[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) a[g] = o0 + g * NW < nout ? Wl[nout * nin + o0 + g * NW] : 0.0f;
+      for (int i = 0; i < nin; ++i) {
+        const float xv = st[(xin + i) * PITCH + col];
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+          if (o0 + g * NW < nout) a[g] = fmaf(Wl[(o0 + g * NW) * nin + i], xv, a[g]);
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (o0 + g * NW < nout) st[(xout + o0 + g * NW) * PITCH + col] = fmaxf(a[g], 0.0f);
+    }
+    __syncthreads();
+  }
+  if (warp == 0 && active) {  // output layer, loss and dL/dz
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float z = W[wofs(4) + 32 + k];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) z = fmaf(W[wofs(4) + k * 8 + i], st[(kX4 + i) * PITCH + col], z);
+      const float yk = (float)((lab >> k) & 1u);
+      const float sig = 1.0f / (1.0f + __expf(-z));
+      if (live) loss += (double)(softplus(z) - yk * z);
+      st[(kD5 + k) * PITCH + col] = live ? (sig - yk) * inv_nS : 0.0f;
+    }
+  }
+  __syncthreads();
+  // backward l = 3..0: delta of layer l's output from the delta above it
+#pragma unroll 1
+  for (int l = 3; l >= 0; --l) {
+    const int nin = wid(l + 1), nup = wid(l + 2);  // this delta's width, the one above
+    const int dup = l == 3 ? kD5 : l == 2 ? kD4 : l == 1 ? kD3 : kD2;
+    const int dout = l == 3 ? kD4 : l == 2 ? kD3 : l == 1 ? kD2 : kD1;
+    const int xact = l == 3 ? kX4 : l == 2 ? kX3 : l == 1 ? kX2 : kX1;
+    const float* Wu = W + wofs(l + 1);  // W_{l+2}[nup][nin]
+#pragma unroll 1
+    for (int i0 = warp; active && i0 < nin; i0 += NW * kG) {
+      float a[kG];
+#pragma unroll
+      for (int g = 0; g < kG; ++g) a[g] = 0.0f;
+      for (int k = 0; k < nup; ++k) {
+        const float dv = st[(dup + k) * PITCH + col];
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+          if (i0 + g * NW < nin) a[g] = fmaf(Wu[k * nin + i0 + g * NW], dv, a[g]);
+      }
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const int i = i0 + g * NW;
+        if (i < nin) st[(dout + i) * PITCH + col] = st[(xact + i) * PITCH + col] > 0.0f ? a[g] : 0.0f;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Gradients of the NP parameters p0, p0 + stride, ... summed over the first
+// `ns` staged samples, each exactly as param_grad forms it (samples in
+// ascending order), as independent chains in one pass over the samples and
+// without branches: a bias gradient is an fma against `ones` (a staged row of
+// 1.0f), which rounds as the plain sum does.  Parameters past kNetParams
+// produce values the caller drops.
+template <int PITCH, int NP>
+__device__ __forceinline__ void param_grads(const float* st, const float* ones, int p0, int stride, int ns,
+                                            float (&out)[NP]) {
+  const float* dp[NP];
+  const float* xp[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int p = min(p0 + q * stride, kNetParams - 1);
+    int l = 4;
+    while (l > 0 && p < wofs(l)) --l;
+    const int nin = wid(l), nout = wid(l + 1);
+    const int r = p - wofs(l);
+    const int drow = (l == 0 ? kD1 : l == 1 ? kD2 : l == 2 ? kD3 : l == 3 ? kD4 : kD5);
+    const int xrow = (l == 0 ? kX0 : l == 1 ? kX1 : l == 2 ? kX2 : l == 3 ? kX3 : kX4);
+    const bool isw = r < nout * nin;
+    dp[q] = st + (drow + (isw ? r / nin : r - nout * nin)) * PITCH;
+    xp[q] = isw ? st + (xrow + r % nin) * PITCH : ones;
+    out[q] = 0.0f;
+  }
+  for (int j = 0; j < ns; ++j) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q] = fmaf(dp[q][j], xp[q][j], out[q]);
+  }
+}
+
 // Gradient of parameter p summed over the first `ns` staged samples:
 // dW = sum delta x (the layer's input), db = sum delta.
 template <int PITCH>

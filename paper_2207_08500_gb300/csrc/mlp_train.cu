@@ -5,8 +5,9 @@
 //
 // Mini-batch Adam is sequential (every step reads the parameters the
 // previous step wrote), so one persistent cluster of CTAs runs all the steps
-// of a call, sharing each step's batch (below).  One thread per sample runs
-// the forward and backward pass (mlp_fb.cuh) against the parameters in
+// of a call, sharing each step's batch (below).  A CTA's four warps share the
+// forward and backward pass of its samples (lane = sample, each layer's
+// outputs split among the warps; mlp_fb.cuh) against the parameters in
 // shared memory.  No launch per step and no global-memory round trip of the
 // parameters; the gradient and the loss are reduced in a fixed order, so a
 // call is deterministic.
@@ -33,8 +34,10 @@ constexpr int kPerCta = (kMaxTrainBatch + kCl - 1) / kCl;    // samples per CTA 
 constexpr int kCPitch = kPerCta + 1;
 constexpr int kSlice = (kNetParams + kCl - 1) / kCl;         // 404 parameters per CTA
 constexpr int kCPer = (kNetParams + kCT - 1) / kCT;          // partial sums per thread
-// floats: W, staging, partial gradient, published slice, Adam m and v
-constexpr int kCOffW = 0, kCOffSt = kNetParams, kCOffPart = kCOffSt + kRows * kCPitch;
+// floats: W, staging (kRows rows, then a row of ones), partial gradient,
+// published slice, Adam m and v
+constexpr int kCOffW = 0, kCOffSt = kNetParams, kCOffOnes = kCOffSt + kRows * kCPitch;
+constexpr int kCOffPart = kCOffOnes + kCPitch;
 constexpr int kCOffSlice = kCOffPart + kNetParams, kCOffM = kCOffSlice + kSlice, kCOffV = kCOffM + kSlice;
 constexpr int kCSmemFloats = kCOffV + kSlice;
 static_assert(kPerCta <= 32 && kSlice <= 4 * kCT, "one warp of samples, four slice entries per thread");
@@ -60,6 +63,7 @@ __global__ void __launch_bounds__(kCT, 1) mlp_train_cluster_kernel(const MlpTrai
   extern __shared__ float sm[];
   float* W = sm + kCOffW;
   float* st = sm + kCOffSt;
+  float* ones = sm + kCOffOnes;
   float* part = sm + kCOffPart;
   float* slice = sm + kCOffSlice;
   float* mm = sm + kCOffM;
@@ -69,6 +73,7 @@ __global__ void __launch_bounds__(kCT, 1) mlp_train_cluster_kernel(const MlpTrai
   const uint32_t rank = cluster_rank();
   const int p_lo = (int)rank * kSlice;
   for (int i = t; i < kNetParams; i += kCT) W[i] = a.params[i];
+  for (int i = t; i < kCPitch; i += kCT) ones[i] = 1.0f;
   for (int i = t; i < kSlice; i += kCT) {
     const int p = p_lo + i;
     mm[i] = p < kNetParams ? a.m[p] : 0.0f;
@@ -86,33 +91,40 @@ __global__ void __launch_bounds__(kCT, 1) mlp_train_cluster_kernel(const MlpTrai
     const int nb = (int)min((long long)a.batch, a.n_perm - s0);
     const int per = (nb + kCl - 1) / kCl;
     const int first = min((int)rank * per, nb), ns = min(per, nb - first);
-    // ---- this CTA's samples: forward and backward (one thread each)
-    if (t < 32) {
-      bool live = t < ns;
+    // ---- this CTA's samples: forward and backward, lane = sample, the four
+    // warps sharing every layer's outputs
+    {
+      const int lane = t & 31, warp = t >> 5;
+      const bool active = lane < kPerCta;  // lanes past kPerCta have no staged column
+      bool live = lane < ns;
       long long idx = 0;
       if (live) {
-        idx = a.perm[s0 + first + t];
+        idx = a.perm[s0 + first + lane];
         if (idx < 0 || idx >= a.n) {
-          bad_index = true;
+          if (warp == 0) bad_index = true;
           live = false;
           idx = 0;
         }
       }
-      if (t < kPerCta) {
-        float xr[6];
+      float xr[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) xr[j] = live ? (float)a.X[idx * 6 + j] : 0.0f;
-        double loss = 0.0;
-        sample_fwd_bwd<kCPitch>(W, st, t, live, xr, live ? a.y[idx] : 0u, 1.0f / (4.0f * (float)nb), loss);
-        loss_sum += loss * (0.25 / (double)nb);
-      }
+      for (int j = 0; j < 6; ++j) xr[j] = live ? (float)a.X[idx * 6 + j] : 0.0f;
+      double loss = 0.0;
+      sample_fwd_bwd_coop<kCPitch, kCT / 32>(W, st, active ? lane : 0, warp, active, live, xr,
+                                             live ? a.y[idx] : 0u, 1.0f / (4.0f * (float)nb), loss);
+      if (warp == 0 && lane < kPerCta) loss_sum += loss * (0.25 / (double)nb);
     }
-    __syncthreads();
-    // ---- partial gradient of every parameter over these samples
+    // ---- partial gradient of every parameter over these samples, four
+    // parameters per pass over the samples
 #pragma unroll 1
-    for (int q = 0; q < kCPer; ++q) {
-      const int p = t + q * kCT;
-      if (p < kNetParams) part[p] = param_grad<kCPitch>(st, p, ns);
+    for (int q = 0; q < kCPer; q += 4) {
+      float g4[4];
+      param_grads<kCPitch, 4>(st, ones, t + q * kCT, kCT, ns, g4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int p = t + (q + u) * kCT;
+        if (p < kNetParams) part[p] = g4[u];
+      }
     }
     cluster_sync();
     // ---- this CTA's slice: sum over the CTAs (rank order), Adam, publish
