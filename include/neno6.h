@@ -178,8 +178,10 @@ int neno6_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
  * kept by the handle.  Device-side conditions (non-physical states) are
  * latched in the status word as for neno6_step.
  * Mixed-precision handles overlap the copies with compute: the state goes in
- * and out in row bands (multiples of 16 rows, at most eight; one band for 1D
- * grids and grids under 512 rows) on a second stream owned by the handle,
+ * and out in row bands (multiples of 16 rows, at most eight: from 1024 rows a
+ * 128-row first and last band around six equal ones, from 256 rows eight
+ * equal bands, else -- and in 1D -- one band) on a second stream owned by the
+ * handle,
  * the first stage's face fluxes and wave-speed maxima start on the bands
  * that have arrived, and the last stage runs band by band, each band copied
  * out as it finishes.  The result is bit for bit that of neno6_step.  U_out

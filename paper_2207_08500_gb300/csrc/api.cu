@@ -396,13 +396,28 @@ int mixed_rhs(neno6_handle* h, const double* U, const double* U0, double* out, i
   return NENO6_OK;
 }
 
-// Row bands of a host-state step on the mixed path: multiples of 16 rows,
-// at most eight (one band for 1D grids and grids under 512 rows).
-int band_rows(const neno6_handle* h) {
+// Row bands of a host-state step on the mixed path, as boundaries
+// b[0] = 0 < b[1] < ... < b[nb] = ny (multiples of 16 but the last); returns
+// nb <= 8.  From 1024 rows a 128-row first and last band around six equal
+// ones: the copy in before the first face kernel and the copy out after the
+// last difference are what the overlap leaves exposed.  From 256 rows eight
+// equal bands; below, and in 1D, one band.
+int band_bounds(const neno6_handle* h, int b[9]) {
   const int ny = h->cfg.ny;
-  int rows = (ny + 7) / 8;
-  rows = (rows + 15) / 16 * 16;
-  return (rows < 64 || h->cfg.ndim == 1) ? ny : rows;
+  int nb = 0;
+  b[nb++] = 0;
+  if (h->cfg.ndim == 2 && ny >= 1024) {
+    constexpr int kEdge = 128;
+    const int last0 = (ny - kEdge) / 16 * 16;
+    const int mid = ((last0 - kEdge + 5) / 6 + 15) / 16 * 16;
+    for (int r = kEdge; r < last0; r += mid) b[nb++] = r;
+    b[nb++] = last0;
+  } else if (h->cfg.ndim == 2 && ny >= 256) {
+    const int rows = ((ny + 7) / 8 + 15) / 16 * 16;
+    for (int r = rows; r < ny; r += rows) b[nb++] = r;
+  }
+  b[nb] = ny;
+  return nb;
 }
 
 int ensure_copy_stream(neno6_handle* h) {
@@ -448,10 +463,10 @@ int mixed_step(neno6_handle* h, double* U, double cfl, double t_end, double* t_d
   double* S1 = h->d_stage;
   double* S2 = h->d_stage + h->state_elems;
   double* tp = t_dev ? t_dev : h->d_t;
-  const int rows = (in_host || out_host) ? band_rows(h) : ny;
-  const int nb = (ny + rows - 1) / rows;
-  auto r0_of = [&](int b) { return b * rows; };
-  auto r1_of = [&](int b) { return b * rows + rows < ny ? b * rows + rows : ny; };
+  int bounds[9] = {0, ny};
+  const int nb = (in_host || out_host) ? band_bounds(h, bounds) : 1;
+  auto r0_of = [&](int b) { return bounds[b]; };
+  auto r1_of = [&](int b) { return bounds[b + 1]; };
   cudaError_t e = cudaSuccess;
   // ---- stage 1: bands in, wave-speed maxima, face fluxes
   fill_faces_args(h, U, nullptr);
