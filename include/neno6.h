@@ -57,7 +57,8 @@ extern "C" {
 
 /* neno6_config.precision */
 #define NENO6_FP64 0        /* everything in binary64 (bit-exact masks)    */
-#define NENO6_MIXED_BF16 1  /* classifier in bf16 on tensor cores, FP32
+#define NENO6_MIXED_BF16 1  /* classifier in bf16 on tensor cores (layer
+                               1's weights as two bf16 terms), FP32
                                reconstruction, FP64 Roe eigenvectors,
                                back-projection, difference and RK3         */
 #define NENO6_MIXED_FP16 2  /* same with fp16 classifier operands          */
