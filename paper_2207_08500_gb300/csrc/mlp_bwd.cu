@@ -9,7 +9,7 @@
 // output delta dL/dz = (sigma(z) - y)/(n S) and the backward deltas, staging
 // every layer's input and delta feature-major in shared memory; then each
 // thread accumulates ~25 of the 3228 parameter gradients over the tile's
-// samples.  Per-CTA partial sums are reduced in a fixed order by a second
+// samples, four per pass (independent chains, each in sample order).  Per-CTA partial sums are reduced in a fixed order by a second
 // kernel, so the result is deterministic.
 #include "internal.h"
 #include "mlp_fb.cuh"
@@ -21,7 +21,7 @@ using namespace mlpfb;
 
 constexpr int kT = 128;        // samples per tile = threads per CTA
 constexpr int kPitch = kT + 1;  // feature-major rows, padded against bank conflicts
-constexpr int kSmemFloats = kNetParams + kRows * kPitch;
+constexpr int kSmemFloats = kNetParams + (kRows + 1) * kPitch;  // W, staged rows, a row of ones
 
 __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ X, const uint8_t* __restrict__ y,
                                                      long long n, const float* __restrict__ params,
@@ -29,8 +29,10 @@ __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ 
   extern __shared__ float sm[];
   float* W = sm;
   float* st = sm + kNetParams;
+  float* ones = st + kRows * kPitch;
   const int t = threadIdx.x;
   for (int i = t; i < kNetParams; i += kT) W[i] = params[i];
+  for (int i = t; i < kPitch; i += kT) ones[i] = 1.0f;
   constexpr int kPer = (kNetParams + kT - 1) / kT;  // parameters owned by this thread
   float acc[kPer];
 #pragma unroll
@@ -47,12 +49,15 @@ __global__ void __launch_bounds__(kT) mlp_bwd_kernel(const double* __restrict__ 
     for (int j = 0; j < 6; ++j) xr[j] = live ? (float)X[s * 6 + j] : 0.0f;
     sample_fwd_bwd<kPitch>(W, st, t, live, xr, live ? y[s] : 0u, inv_nS, loss);
     __syncthreads();
-    // ---- parameter gradients over the tile: dW = delta^T x, db = sum delta
+    // ---- parameter gradients over the tile: dW = delta^T x, db = sum delta,
+    // four parameters per pass over the samples
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int p = t + q * kT;
-      if (p >= kNetParams) break;
-      acc[q] += param_grad<kPitch>(st, p, kT);
+    for (int q = 0; q < kPer; q += 4) {
+      float g4[4];
+      param_grads<kPitch, 4>(st, ones, t + q * kT, kT, kT, g4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q + u < kPer) acc[q + u] += g4[u];
     }
     __syncthreads();
   }
