@@ -53,3 +53,36 @@ def test_flip_stats_counts():
     assert s["flips"] == 2 and s["flips_outside_band"] == 0 and s["rows_in_band"] == 1.0
     s = ws.flip_stats(z64, z16, 0.05)
     assert s["flips_outside_band"] == 2 and s["rows_in_band"] == 0.0
+
+
+def test_bf16_layer1_split_keeps_smooth_stencils_out_of_the_band():
+    """Why the bf16 tensor-core image carries layer 1's weights as two bf16
+    terms: on smooth stencils (a mean plus a variation of 1e-3 per cell) the
+    first layer's weights nearly cancel against the mean, and one bf16
+    rounding of W1 leaves a residue larger than the variation.  With the
+    split (the emulation `forward16` follows the kernel) the logits stay
+    closer to FP64 and far fewer rows fall into the guard band or flip."""
+    import paper_2207_08500_gb300 as p
+    net = Net.load(p.DEFAULT_WEIGHTS)
+    rng = np.random.default_rng(5)
+    n = 20000
+    X = rng.uniform(-1, 1, (n, 1)) + rng.uniform(-1e-3, 1e-3, (n, 1)) * np.arange(6)[None, :]
+    z64 = ws.forward64(net, X)
+    z_split = ws.forward16(net, X, "bf16")
+    rnd = ws.ROUND["bf16"]
+    a = rnd(ws.normalise32(X))  # the same evaluation with W1 rounded once
+    for li, (W, b) in enumerate(net.layers):
+        if li + 1 < len(net.layers):
+            h = np.maximum(a @ rnd(W.astype(np.float32)).T + b.astype(np.float32), np.float32(0.0))
+            a = rnd(h) if li + 2 < len(net.layers) else h
+        else:
+            a = a @ W.astype(np.float32).T + b.astype(np.float32)
+    z_single = a
+    err_split, err_single = np.abs(z_split - z64), np.abs(z_single - z64)
+    band_split = (np.abs(z_split) < 1.0).any(axis=1).mean()
+    band_single = (np.abs(z_single) < 1.0).any(axis=1).mean()
+    flips_split = ((z_split > 0) != (z64 > 0)).sum()
+    flips_single = ((z_single > 0) != (z64 > 0)).sum()
+    assert np.median(err_single) > 1.5 * np.median(err_split)
+    assert band_single > 3 * band_split
+    assert flips_single > 5 * flips_split
