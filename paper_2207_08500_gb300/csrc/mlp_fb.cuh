@@ -230,11 +230,12 @@ __device__ __forceinline__ void sample_fwd_bwd_coop(const float* W, float* st, i
 }
 
 // Gradients of the NP parameters p0, p0 + stride, ... summed over the first
-// `ns` staged samples, each exactly as param_grad forms it (samples in
-// ascending order), as independent chains in one pass over the samples and
-// without branches: a bias gradient is an fma against `ones` (a staged row of
-// 1.0f), which rounds as the plain sum does.  Parameters past kNetParams
-// produce values the caller drops.
+// `ns` staged samples -- dW = sum delta x (x the layer's input), db = sum
+// delta, each an fma chain over the samples in ascending order -- as
+// independent chains in one pass over the samples and without branches: a
+// bias gradient is an fma against `ones` (a staged row of 1.0f), which rounds
+// as the plain sum does.  Parameters past kNetParams produce values the
+// caller drops.
 template <int PITCH, int NP>
 __device__ __forceinline__ void param_grads(const float* st, const float* ones, int p0, int stride, int ns,
                                             float (&out)[NP]) {
@@ -258,28 +259,6 @@ __device__ __forceinline__ void param_grads(const float* st, const float* ones, 
 #pragma unroll
     for (int q = 0; q < NP; ++q) out[q] = fmaf(dp[q][j], xp[q][j], out[q]);
   }
-}
-
-// Gradient of parameter p summed over the first `ns` staged samples:
-// dW = sum delta x (the layer's input), db = sum delta.
-template <int PITCH>
-__device__ __forceinline__ float param_grad(const float* st, int p, int ns) {
-  int l = 4;
-  while (l > 0 && p < wofs(l)) --l;
-  const int nin = wid(l), nout = wid(l + 1);
-  const int r = p - wofs(l);
-  const int drow = (l == 0 ? kD1 : l == 1 ? kD2 : l == 2 ? kD3 : l == 3 ? kD4 : kD5);
-  const int xrow = (l == 0 ? kX0 : l == 1 ? kX1 : l == 2 ? kX2 : l == 3 ? kX3 : kX4);
-  float a = 0.0f;
-  if (r < nout * nin) {
-    const float* dp = st + (drow + r / nin) * PITCH;
-    const float* xp = st + (xrow + r % nin) * PITCH;
-    for (int j = 0; j < ns; ++j) a = fmaf(dp[j], xp[j], a);
-  } else {
-    const float* dp = st + (drow + (r - nout * nin)) * PITCH;
-    for (int j = 0; j < ns; ++j) a += dp[j];
-  }
-  return a;
 }
 
 }  // namespace mlpfb
